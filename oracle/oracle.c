@@ -1,0 +1,364 @@
+/*
+ * oracle.c -- plain FP64 reference of the CT augmentation hot path.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the checker the CUDA library is
+ * compared against: it is compiled into liboracle.so and called from the test
+ * suite, from __graft_entry__.smoke() and from the benchmark's CPU-baseline
+ * leg, never from the product path.  It shares no code, header, table or
+ * constant generator with the CUDA library.
+ *
+ * Everything is single threaded, unblocked and computed in double precision
+ * directly from the definitions:
+ *
+ *   coordinate   s = A o + b                          (Sec. 4, x' = Ax + b)
+ *   image        trilinear interpolation of the input,
+ *                every tap outside the volume reads the fill value
+ *                                                     (Sec. 4, texture sampling)
+ *   label        nearest voxel, floor(s + 1/2), fill label outside
+ *                                                     (Sec. 4, nearest neighbour)
+ *   intensity    y = a v + beta + sigma n,  n ~ N(0, 1) (Sec. 4, additive noise)
+ *   noise        Philox4x32-10 (Salmon et al., SC'11) + Box-Muller
+ *   adjoint      d(out)/d(input) and d(out)/d(T) of the above
+ *   IOU loss     1 - |py|_1 / (|p|_1 + |y|_1 - |py|_1), per class
+ *                                                     (Sec. 5.C, IOU loss)
+ *
+ * Conventions: volumes are [nz][ny][nx], x fastest.  An output index
+ * o = (i, j, k) maps to the input coordinate s_r = T[r][0] i + T[r][1] j +
+ * T[r][2] k + T[r][3] (r = x, y, z; T row-major 3x4, float32 promoted exactly
+ * to double).  Voxel centres sit at integer coordinates.
+ *
+ * Noise: output voxels are grouped in quads of four z-consecutive voxels,
+ * quad index Q = ((k >> 2) * ony + j) * onx + i, lane l = k & 3.  One
+ * Philox4x32-10 call with key (lo32(seed), hi32(seed)) and counter
+ * (lo32(Q), hi32(Q), noise_id, 0) gives words r0..r3; lanes 0,1 use the pair
+ * (r0, r1), lanes 2,3 the pair (r2, r3).  With u1 = ((ra >> 8) + 1/2) 2^-24 and
+ * u2 = (rb >> 8) 2^-24, R = sqrt(-2 ln u1); even lanes take R cos(2 pi u2), odd
+ * lanes R sin(2 pi u2).
+ */
+#include <math.h>
+#include <stddef.h>
+#include <stdint.h>
+#include <string.h>
+
+#define ORACLE_EXPORT __attribute__((visibility("default")))
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10, from the published round function:                         */
+/*   (hi0, lo0) = M0 * c0,  (hi1, lo1) = M1 * c2   (32x32 -> 64 bit)        */
+/*   c <- (hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0)                            */
+/* with the key advanced by the Weyl constants between rounds.               */
+/* ------------------------------------------------------------------------ */
+ORACLE_EXPORT void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2],
+                                        uint32_t out[4]) {
+  const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+  const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+  uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+  uint32_t k0 = key[0], k1 = key[1];
+  for (int round = 0; round < 10; ++round) {
+    if (round > 0) {
+      k0 += W0;
+      k1 += W1;
+    }
+    uint64_t p0 = (uint64_t)M0 * (uint64_t)c0;
+    uint64_t p1 = (uint64_t)M1 * (uint64_t)c2;
+    uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+    uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+    uint32_t n0 = hi1 ^ c1 ^ k0;
+    uint32_t n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+  }
+  out[0] = c0;
+  out[1] = c1;
+  out[2] = c2;
+  out[3] = c3;
+}
+
+/* Philox words for n counters (n x 4 words in, n x 4 words out). */
+ORACLE_EXPORT void oracle_philox_many(uint64_t seed, const uint32_t* ctrs, int64_t n,
+                                      uint32_t* out) {
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  for (int64_t q = 0; q < n; ++q) oracle_philox4x32_10(ctrs + 4 * q, key, out + 4 * q);
+}
+
+/* Standard normal for output voxel (i, j, k) of a volume (see header). */
+static double noise_normal(uint64_t seed, uint32_t noise_id, int64_t onx, int64_t ony,
+                           int64_t i, int64_t j, int64_t k) {
+  const double two_m24 = 1.0 / 16777216.0;
+  const double pi = 3.14159265358979323846;
+  uint64_t quad = (uint64_t)(((k >> 2) * ony + j) * onx + i);
+  uint32_t ctr[4] = {(uint32_t)quad, (uint32_t)(quad >> 32), noise_id, 0u};
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  uint32_t r[4];
+  oracle_philox4x32_10(ctr, key, r);
+  int lane = (int)(k & 3);
+  uint32_t ra = (lane < 2) ? r[0] : r[2];
+  uint32_t rb = (lane < 2) ? r[1] : r[3];
+  double u1 = ((double)(ra >> 8) + 0.5) * two_m24;
+  double u2 = (double)(rb >> 8) * two_m24;
+  double radius = sqrt(-2.0 * log(u1));
+  return (lane & 1) ? radius * sin(2.0 * pi * u2) : radius * cos(2.0 * pi * u2);
+}
+
+/* Standard normals for a list of flattened output indices q = (k*ony+j)*onx+i. */
+ORACLE_EXPORT void oracle_noise(uint64_t seed, uint32_t noise_id, int64_t onx, int64_t ony,
+                                const int64_t* q, int64_t n, double* z) {
+  for (int64_t m = 0; m < n; ++m) {
+    int64_t i = q[m] % onx, j = (q[m] / onx) % ony, k = q[m] / (onx * ony);
+    z[m] = noise_normal(seed, noise_id, onx, ony, i, j, k);
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sampling                                                                  */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  const void* image;
+  int image_is_i16;
+  const uint8_t* label;
+  int64_t nx, ny, nz;
+  int64_t onx, ony, onz;
+  double T[3][4];
+  double a, beta, sigma, fill;
+  int fill_label;
+  uint64_t seed;
+  uint32_t noise_id;
+} volume;
+
+static void load_volume(volume* v, const void* image, int image_is_i16, const uint8_t* label,
+                        int64_t nx, int64_t ny, int64_t nz, int64_t onx, int64_t ony,
+                        int64_t onz, const float* T12, float a, float beta, float sigma,
+                        float fill, int fill_label, uint64_t seed, uint32_t noise_id) {
+  v->image = image;
+  v->image_is_i16 = image_is_i16;
+  v->label = label;
+  v->nx = nx;
+  v->ny = ny;
+  v->nz = nz;
+  v->onx = onx;
+  v->ony = ony;
+  v->onz = onz;
+  for (int r = 0; r < 3; ++r)
+    for (int c = 0; c < 4; ++c) v->T[r][c] = (double)T12[4 * r + c];
+  v->a = a;
+  v->beta = beta;
+  v->sigma = sigma;
+  v->fill = fill;
+  v->fill_label = fill_label;
+  v->seed = seed;
+  v->noise_id = noise_id;
+}
+
+static int in_volume(const volume* v, int64_t x, int64_t y, int64_t z) {
+  return x >= 0 && y >= 0 && z >= 0 && x < v->nx && y < v->ny && z < v->nz;
+}
+
+/* V(n): input value at integer position n, or the fill value outside. */
+static double image_at(const volume* v, int64_t x, int64_t y, int64_t z) {
+  if (!in_volume(v, x, y, z)) return v->fill;
+  size_t idx = ((size_t)z * (size_t)v->ny + (size_t)y) * (size_t)v->nx + (size_t)x;
+  if (v->image_is_i16) return (double)((const int16_t*)v->image)[idx];
+  return (double)((const float*)v->image)[idx];
+}
+
+static void coordinate(const volume* v, int64_t i, int64_t j, int64_t k, double s[3]) {
+  for (int r = 0; r < 3; ++r)
+    s[r] = v->T[r][0] * (double)i + v->T[r][1] * (double)j + v->T[r][2] * (double)k +
+           v->T[r][3];
+}
+
+/* Trilinear interpolation: sum over the 8 corners d of the cell floor(s) of
+ * prod_r (d_r ? t_r : 1 - t_r) * V(floor(s) + d). */
+static double trilinear(const volume* v, const double s[3]) {
+  double f[3], t[3];
+  for (int r = 0; r < 3; ++r) {
+    f[r] = floor(s[r]);
+    t[r] = s[r] - f[r];
+  }
+  double acc = 0.0;
+  for (int d = 0; d < 8; ++d) {
+    int dx = d & 1, dy = (d >> 1) & 1, dz = (d >> 2) & 1;
+    double w = (dx ? t[0] : 1.0 - t[0]) * (dy ? t[1] : 1.0 - t[1]) * (dz ? t[2] : 1.0 - t[2]);
+    acc += w * image_at(v, (int64_t)f[0] + dx, (int64_t)f[1] + dy, (int64_t)f[2] + dz);
+  }
+  return acc;
+}
+
+static int nearest_label(const volume* v, const double s[3]) {
+  int64_t n[3];
+  for (int r = 0; r < 3; ++r) n[r] = (int64_t)floor(s[r] + 0.5);
+  if (!in_volume(v, n[0], n[1], n[2])) return v->fill_label;
+  size_t idx = ((size_t)n[2] * (size_t)v->ny + (size_t)n[1]) * (size_t)v->nx + (size_t)n[0];
+  return v->label[idx];
+}
+
+static int near_tie(const double s[3]) {
+  for (int r = 0; r < 3; ++r)
+    if (fabs(s[r] - floor(s[r]) - 0.5) < 1e-5) return 1;
+  return 0;
+}
+
+static void one_voxel(const volume* v, int64_t i, int64_t j, int64_t k, double* out_val,
+                      uint8_t* out_lab, uint8_t* tie) {
+  double s[3];
+  coordinate(v, i, j, k, s);
+  if (out_val) {
+    double val = v->a * trilinear(v, s) + v->beta;
+    if (v->sigma != 0.0)
+      val += v->sigma * noise_normal(v->seed, v->noise_id, v->onx, v->ony, i, j, k);
+    *out_val = val;
+  }
+  if (out_lab) *out_lab = (uint8_t)nearest_label(v, s);
+  if (tie) *tie = (uint8_t)near_tie(s);
+}
+
+/* Forward warp of one volume over its whole output grid.  Any of out_image,
+ * out_label, tie may be NULL.  Returns the number of label-tie voxels (source
+ * coordinate within 1e-5 of a rounding tie on some axis). */
+ORACLE_EXPORT int64_t oracle_warp_fwd(const void* image, int image_is_i16,
+                                      const uint8_t* label, int64_t nx, int64_t ny,
+                                      int64_t nz, int64_t onx, int64_t ony, int64_t onz,
+                                      const float* T12, float a, float beta, float sigma,
+                                      float fill, int fill_label, uint64_t seed,
+                                      uint32_t noise_id, double* out_image,
+                                      uint8_t* out_label, uint8_t* tie) {
+  volume v;
+  load_volume(&v, image, image_is_i16, label, nx, ny, nz, onx, ony, onz, T12, a, beta, sigma,
+              fill, fill_label, seed, noise_id);
+  int64_t ties = 0;
+  size_t q = 0;
+  for (int64_t k = 0; k < onz; ++k)
+    for (int64_t j = 0; j < ony; ++j)
+      for (int64_t i = 0; i < onx; ++i, ++q) {
+        uint8_t tflag = 0;
+        one_voxel(&v, i, j, k, out_image ? out_image + q : NULL,
+                  (out_label && label) ? out_label + q : NULL, &tflag);
+        if (tie) tie[q] = tflag;
+        ties += tflag;
+      }
+  return ties;
+}
+
+/* Forward warp evaluated only at the listed flattened output indices. */
+ORACLE_EXPORT void oracle_warp_fwd_points(const void* image, int image_is_i16,
+                                          const uint8_t* label, int64_t nx, int64_t ny,
+                                          int64_t nz, int64_t onx, int64_t ony, int64_t onz,
+                                          const float* T12, float a, float beta, float sigma,
+                                          float fill, int fill_label, uint64_t seed,
+                                          uint32_t noise_id, const int64_t* q, int64_t n,
+                                          double* out_image, uint8_t* out_label,
+                                          uint8_t* tie) {
+  volume v;
+  load_volume(&v, image, image_is_i16, label, nx, ny, nz, onx, ony, onz, T12, a, beta, sigma,
+              fill, fill_label, seed, noise_id);
+  for (int64_t m = 0; m < n; ++m) {
+    int64_t i = q[m] % onx, j = (q[m] / onx) % ony, k = q[m] / (onx * ony);
+    one_voxel(&v, i, j, k, out_image ? out_image + m : NULL,
+              (out_label && label) ? out_label + m : NULL, tie ? tie + m : NULL);
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Adjoint of the image warp.                                                */
+/*   out(o) = a * sum_d w_d(o) V(f(o) + d) + beta (+ noise, independent of   */
+/*   the input and of T).  With g the upstream gradient:                     */
+/*   grad_in[n]  = sum_o a g(o) w_d(o)      over in-volume taps n = f(o) + d */
+/*   dv/ds_r     = sum_d (d_r ? +1 : -1) prod_{q != r} (d_q ? t_q : 1 - t_q)  */
+/*                 V(f + d)     (right derivative where s_r is an integer)   */
+/*   grad_T[r][c] = sum_o a g(o) dv/ds_r(o) obar_c(o), obar = (i, j, k, 1).  */
+/* Fill taps contribute to dv/ds but not to grad_in.                         */
+/* grad_in (input shape, overwritten), grad_T (12) and dvds (3 per output     */
+/* voxel) may each be NULL.                                                  */
+/* ------------------------------------------------------------------------ */
+ORACLE_EXPORT void oracle_warp_bwd(const void* image, int image_is_i16, int64_t nx,
+                                   int64_t ny, int64_t nz, int64_t onx, int64_t ony,
+                                   int64_t onz, const float* T12, float a, float fill,
+                                   const float* g, double* grad_in, double* grad_T,
+                                   double* dvds) {
+  volume v;
+  load_volume(&v, image, image_is_i16, NULL, nx, ny, nz, onx, ony, onz, T12, a, 0.0f, 0.0f,
+              fill, 0, 0, 0);
+  if (grad_in) memset(grad_in, 0, sizeof(double) * (size_t)(nx * ny * nz));
+  double gt[3][4] = {{0}};
+  size_t q = 0;
+  for (int64_t k = 0; k < onz; ++k)
+    for (int64_t j = 0; j < ony; ++j)
+      for (int64_t i = 0; i < onx; ++i, ++q) {
+        double s[3], f[3], t[3];
+        coordinate(&v, i, j, k, s);
+        for (int r = 0; r < 3; ++r) {
+          f[r] = floor(s[r]);
+          t[r] = s[r] - f[r];
+        }
+        double ga = v.a * (double)g[q];
+        double dv[3] = {0.0, 0.0, 0.0};
+        for (int d = 0; d < 8; ++d) {
+          int dd[3] = {d & 1, (d >> 1) & 1, (d >> 2) & 1};
+          double wt[3];
+          for (int r = 0; r < 3; ++r) wt[r] = dd[r] ? t[r] : 1.0 - t[r];
+          int64_t x = (int64_t)f[0] + dd[0], y = (int64_t)f[1] + dd[1],
+                  z = (int64_t)f[2] + dd[2];
+          double val = image_at(&v, x, y, z);
+          for (int r = 0; r < 3; ++r) {
+            double w_other = 1.0;
+            for (int p = 0; p < 3; ++p)
+              if (p != r) w_other *= wt[p];
+            dv[r] += (dd[r] ? 1.0 : -1.0) * w_other * val;
+          }
+          if (grad_in && in_volume(&v, x, y, z))
+            grad_in[((size_t)z * (size_t)ny + (size_t)y) * (size_t)nx + (size_t)x] +=
+                ga * wt[0] * wt[1] * wt[2];
+        }
+        double obar[4] = {(double)i, (double)j, (double)k, 1.0};
+        for (int r = 0; r < 3; ++r)
+          for (int c = 0; c < 4; ++c) gt[r][c] += ga * dv[r] * obar[c];
+        if (dvds)
+          for (int r = 0; r < 3; ++r) dvds[3 * q + r] = dv[r];
+      }
+  if (grad_T)
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 4; ++c) grad_T[4 * r + c] = gt[r][c];
+}
+
+/* ------------------------------------------------------------------------ */
+/* Soft IOU loss of one volume (Sec. 5.C).                                   */
+/* p: [C][nvox] probabilities, y: [nvox] labels in 0..C-1 (other values      */
+/* belong to no class).  For each class c, with y_k = [label_k == c]:        */
+/*   I = sum p y, P = sum p, Y = sum y, U = P + Y - I,                       */
+/*   L_c = 1 - I / U   (U = 0: L_c = 0, the score of an empty prediction of  */
+/*                      an empty class being 1),                             */
+/*   dL_c/dp_k = y_k ? -1/U : I/U^2   (0 where U = 0),                        */
+/* grad[c][k] = grad_scale * dL_c/dp_k (double).  sums: [C][3] = (I, P, Y);  */
+/* loss_c: [C].  grad and sums may be NULL.                                  */
+/* ------------------------------------------------------------------------ */
+ORACLE_EXPORT void oracle_iou(const float* p, const uint8_t* y, int n_classes, int64_t nvox,
+                              double grad_scale, double* loss_c, double* sums, double* grad) {
+  for (int c = 0; c < n_classes; ++c) {
+    const float* pc = p + (size_t)c * (size_t)nvox;
+    double I = 0.0, P = 0.0, Y = 0.0;
+    for (int64_t k = 0; k < nvox; ++k) {
+      double pk = (double)pc[k];
+      double yk = (y[k] == c) ? 1.0 : 0.0;
+      I += pk * yk;
+      P += pk;
+      Y += yk;
+    }
+    double U = P + Y - I;
+    loss_c[c] = (U > 0.0) ? 1.0 - I / U : 0.0;
+    if (sums) {
+      sums[3 * c + 0] = I;
+      sums[3 * c + 1] = P;
+      sums[3 * c + 2] = Y;
+    }
+    if (grad) {
+      double* gc = grad + (size_t)c * (size_t)nvox;
+      for (int64_t k = 0; k < nvox; ++k) {
+        double d = 0.0;
+        if (U > 0.0) d = (y[k] == c) ? -1.0 / U : I / (U * U);
+        gc[k] = grad_scale * d;
+      }
+    }
+  }
+}

@@ -1,0 +1,175 @@
+"""Python entry points of the FP64 oracle (ctypes over liboracle.so).
+
+TEST INFRASTRUCTURE ONLY -- used by tests, ``smoke()`` and the benchmark's
+CPU baseline, never by the product path.
+
+Inputs are numpy arrays (torch tensors are converted with ``.cpu().numpy()``);
+volume records are any object with the fields of ``synth.workloads.VolumeCase``.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+_lock = threading.Lock()
+
+_i64, _u64, _u32, _f32, _int = C.c_int64, C.c_uint64, C.c_uint32, C.c_float, C.c_int
+_vp = C.c_void_p
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = C.CDLL(path)
+            L.oracle_philox4x32_10.argtypes = [_vp, _vp, _vp]
+            L.oracle_philox_many.argtypes = [_u64, _vp, _i64, _vp]
+            L.oracle_noise.argtypes = [_u64, _u32, _i64, _i64, _vp, _i64, _vp]
+            fwd_args = [_vp, _int, _vp, _i64, _i64, _i64, _i64, _i64, _i64, _vp, _f32, _f32,
+                        _f32, _f32, _int, _u64, _u32]
+            L.oracle_warp_fwd.argtypes = fwd_args + [_vp, _vp, _vp]
+            L.oracle_warp_fwd.restype = _i64
+            L.oracle_warp_fwd_points.argtypes = fwd_args + [_vp, _i64, _vp, _vp, _vp]
+            L.oracle_warp_bwd.argtypes = [_vp, _int, _i64, _i64, _i64, _i64, _i64, _i64, _vp,
+                                          _f32, _f32, _vp, _vp, _vp, _vp]
+            L.oracle_iou.argtypes = [_vp, _vp, _int, _i64, C.c_double, _vp, _vp, _vp]
+            _lib = L
+    return _lib
+
+
+def _np(x, dtype=None):
+    if x is None:
+        return None
+    if hasattr(x, "detach"):
+        x = x.detach().cpu().numpy()
+    x = np.ascontiguousarray(x)
+    if dtype is not None and x.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {x.dtype}")
+    return x
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(_vp)
+
+
+def philox(ctrs, seed: int):
+    """Philox4x32-10 words for counters ``ctrs`` ([n, 4] uint32), key from ``seed``."""
+    c = _np(np.asarray(ctrs, dtype=np.uint32).reshape(-1, 4), np.uint32)
+    out = np.empty_like(c)
+    lib().oracle_philox_many(_u64(seed), _ptr(c), c.shape[0], _ptr(out))
+    return out
+
+
+def noise(seed: int, noise_id: int, onx: int, ony: int, q):
+    """Standard normals of the flattened output indices ``q``."""
+    q = _np(np.asarray(q, dtype=np.int64), np.int64)
+    z = np.empty(q.shape, dtype=np.float64)
+    lib().oracle_noise(_u64(seed), _u32(noise_id), onx, ony, _ptr(q), q.size, _ptr(z))
+    return z
+
+
+def _vol_args(v, seed):
+    img = _np(v.image)
+    if img.dtype not in (np.float32, np.int16):
+        raise TypeError("image must be float32 or int16")
+    lab = _np(v.label, np.uint8) if v.label is not None else None
+    nz, ny, nx = img.shape
+    onx, ony, onz = v.out_shape
+    T = np.ascontiguousarray(np.asarray(v.T, dtype=np.float32).reshape(12))
+    keep = (img, lab, T)
+    args = [_ptr(img), int(img.dtype == np.int16), _ptr(lab), nx, ny, nz, onx, ony, onz,
+            _ptr(T), _f32(v.photo_a), _f32(v.photo_b), _f32(v.sigma), _f32(v.fill_image),
+            int(v.fill_label), _u64(seed), _u32(v.noise_id)]
+    return args, keep
+
+
+def warp_fwd(v, seed: int, want_image=True, want_label=True):
+    """Whole-grid forward warp of one volume.
+
+    Returns ``(image f64 [onz, ony, onx] or None, label u8 or None,
+    tie u8 flags, n_ties)``."""
+    args, keep = _vol_args(v, seed)
+    onx, ony, onz = v.out_shape
+    out = np.empty((onz, ony, onx), np.float64) if want_image else None
+    lab = (np.empty((onz, ony, onx), np.uint8)
+           if (want_label and v.label is not None) else None)
+    tie = np.empty((onz, ony, onx), np.uint8)
+    n = lib().oracle_warp_fwd(*args, _ptr(out), _ptr(lab), _ptr(tie))
+    del keep
+    return out, lab, tie, int(n)
+
+
+def warp_fwd_points(v, seed: int, q):
+    """Forward warp at flattened output indices ``q``: (values f64, labels u8, ties u8)."""
+    args, keep = _vol_args(v, seed)
+    q = _np(np.asarray(q, dtype=np.int64), np.int64)
+    vals = np.empty(q.shape, np.float64)
+    labs = np.empty(q.shape, np.uint8) if v.label is not None else None
+    ties = np.empty(q.shape, np.uint8)
+    lib().oracle_warp_fwd_points(*args, _ptr(q), q.size, _ptr(vals), _ptr(labs), _ptr(ties))
+    del keep
+    return vals, labs, ties
+
+
+def warp_bwd(v, g, want_grad_in=True, want_dvds=False):
+    """Adjoint of the image warp of one volume for upstream gradient ``g``
+    (output shape).  Returns ``(grad_in f64 or None, grad_T f64 [3, 4],
+    dvds f64 [onz, ony, onx, 3] or None)``."""
+    img = _np(v.image)
+    nz, ny, nx = img.shape
+    onx, ony, onz = v.out_shape
+    g = _np(g, np.float32)
+    assert g.size == onx * ony * onz
+    T = np.ascontiguousarray(np.asarray(v.T, dtype=np.float32).reshape(12))
+    gi = np.empty((nz, ny, nx), np.float64) if want_grad_in else None
+    gt = np.empty(12, np.float64)
+    dv = np.empty((onz, ony, onx, 3), np.float64) if want_dvds else None
+    lib().oracle_warp_bwd(_ptr(img), int(img.dtype == np.int16), nx, ny, nz, onx, ony, onz,
+                          _ptr(T), _f32(v.photo_a), _f32(v.fill_image), _ptr(g), _ptr(gi),
+                          _ptr(gt), _ptr(dv))
+    return gi, gt.reshape(3, 4), dv
+
+
+def iou(p, y, n_classes: int, grad_scale: float = 1.0, want_grad=True):
+    """Soft IOU loss of one volume.  ``p``: [C, nvox] float32, ``y``: [nvox]
+    uint8.  Returns ``(loss_c [C], sums [C, 3] = (I, P, Y), grad [C, nvox] or None)``."""
+    p = _np(p, np.float32).reshape(n_classes, -1)
+    y = _np(y, np.uint8).reshape(-1)
+    nvox = y.size
+    assert p.shape[1] == nvox
+    loss = np.empty(n_classes, np.float64)
+    sums = np.empty((n_classes, 3), np.float64)
+    grad = np.empty((n_classes, nvox), np.float64) if want_grad else None
+    lib().oracle_iou(_ptr(p), _ptr(y), n_classes, nvox, C.c_double(grad_scale), _ptr(loss),
+                     _ptr(sums), _ptr(grad))
+    return loss, sums, grad
+
+
+def warp_iou(vols, p_packed, n_classes: int, want_grad=True):
+    """Label warp followed by the IOU loss, batch-averaged (Sec. 5.C: mean over
+    classes, then over the batch).  ``p_packed`` holds per volume
+    ``[C][onz][ony][onx]`` consecutively.  Returns ``(loss [B], grad packed f64
+    or None, sums [B, C, 3])`` where ``grad`` is the gradient of the batch mean."""
+    p = _np(p_packed, np.float32).reshape(-1)
+    B = len(vols)
+    scale = 1.0 / (B * n_classes)
+    losses, sums, grads = [], [], []
+    off = 0
+    for v in vols:
+        nvox = v.n_out
+        _, lab, _, _ = warp_fwd(v, 0, want_image=False, want_label=True)
+        pc = p[off: off + n_classes * nvox].reshape(n_classes, nvox)
+        lc, sc, gc = iou(pc, lab.reshape(-1), n_classes, scale, want_grad)
+        losses.append(lc.mean())
+        sums.append(sc)
+        if want_grad:
+            grads.append(gc.reshape(-1))
+        off += n_classes * nvox
+    grad = np.concatenate(grads) if want_grad else None
+    return np.asarray(losses), grad, np.asarray(sums)
