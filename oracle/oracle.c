@@ -31,9 +31,9 @@
  * quad index Q = ((k >> 2) * ony + j) * onx + i, lane l = k & 3.  One
  * Philox4x32-10 call with key (lo32(seed), hi32(seed)) and counter
  * (lo32(Q), hi32(Q), noise_id, 0) gives words r0..r3; lanes 0,1 use the pair
- * (r0, r1), lanes 2,3 the pair (r2, r3).  With u1 = ((ra >> 8) + 1/2) 2^-24 and
- * u2 = (rb >> 8) 2^-24, R = sqrt(-2 ln u1); even lanes take R cos(2 pi u2), odd
- * lanes R sin(2 pi u2).
+ * (r0, r1), lanes 2,3 the pair (r2, r3).  With u1 = ((ra >> 8) + 1) 2^-24 in
+ * (0, 1] and u2 = (rb >> 8) 2^-24 in [0, 1) (both exact in float32),
+ * R = sqrt(-2 ln u1); even lanes take R cos(2 pi u2), odd lanes R sin(2 pi u2).
  */
 #include <math.h>
 #include <stddef.h>
@@ -96,7 +96,7 @@ static double noise_normal(uint64_t seed, uint32_t noise_id, int64_t onx, int64_
   int lane = (int)(k & 3);
   uint32_t ra = (lane < 2) ? r[0] : r[2];
   uint32_t rb = (lane < 2) ? r[1] : r[3];
-  double u1 = ((double)(ra >> 8) + 0.5) * two_m24;
+  double u1 = ((double)(ra >> 8) + 1.0) * two_m24;
   double u2 = (double)(rb >> 8) * two_m24;
   double radius = sqrt(-2.0 * log(u1));
   return (lane & 1) ? radius * sin(2.0 * pi * u2) : radius * cos(2.0 * pi * u2);

@@ -65,8 +65,8 @@ def test_noise_moments(normals):
     assert abs(z.var() - 1.0) < 5.0 * np.sqrt(2.0 / n)
     kurt = np.mean(z ** 4) / np.mean(z ** 2) ** 2
     assert abs(kurt - 3.0) < 5.0 * np.sqrt(24.0 / n)
-    # Box-Muller with 24-bit u1 bounds |z| by sqrt(-2 ln 2^-25) = 5.887.
-    assert np.abs(z).max() <= np.sqrt(-2.0 * np.log(2.0 ** -25)) + 1e-12
+    # Box-Muller with u1 >= 2^-24 bounds |z| by sqrt(-2 ln 2^-24) = 5.77.
+    assert np.abs(z).max() <= np.sqrt(-2.0 * np.log(2.0 ** -24)) + 1e-12
 
 
 def test_noise_ks(normals):
