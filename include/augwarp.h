@@ -1,0 +1,217 @@
+/*
+ * augwarp.h -- C ABI of the B300 (sm_103a) CT data-augmentation library.
+ *
+ * The library implements the GPU augmentation path of Rister et al., "CT organ
+ * segmentation using GPU data augmentation, unsupervised labels and IOU loss"
+ * (arXiv 1811.11226):
+ *
+ *   - Sec. 4: each output voxel o = (i, j, k) of a crop is mapped through an
+ *     affine coordinate map s = A o + b, the image is sampled trilinearly at s
+ *     and the label volume at the nearest voxel, a constant fill is used
+ *     outside the input, and additive Gaussian noise is applied;
+ *   - the intensity affine y = a v + beta precedes the noise;
+ *   - the adjoint of the image warp with respect to the input volume and the
+ *     12 affine parameters (the paper has no backward pass; it is what makes
+ *     the warp trainable);
+ *   - Sec. 5.C: the soft IOU loss 1 - |py|_1 / (|p|_1 + |y|_1 - |py|_1),
+ *     averaged over classes and over the batch, fused with the nearest-label
+ *     warp so the warped labels never reach memory.
+ *
+ * Conventions (all entry points):
+ *   - Volumes are dense, C-contiguous [nz][ny][nx] arrays, x fastest.
+ *   - The affine is float32 row-major 3x4 T in voxel-index units:
+ *       s_r = T[r][0] i + T[r][1] j + T[r][2] k + T[r][3],  r = x, y, z.
+ *     Voxel centres are at integer coordinates.
+ *   - Image sample: trilinear over the cell floor(s); every tap outside the
+ *     input reads fill_image.  Label sample: input label at floor(s + 1/2),
+ *     fill_label outside.
+ *   - Output value: y = photo_a * v + photo_b + noise_sigma * n, with n a
+ *     standard normal from Philox4x32-10 (key = seed, counter = (quad index,
+ *     noise_id)) and Box-Muller; quads are four z-consecutive output voxels
+ *     (k = 4m..4m+3) -- see aug_warp_fwd.
+ *   - All pointers are DEVICE pointers unless stated otherwise.  The caller
+ *     owns every buffer; the library allocates no device memory in any entry
+ *     point.  Every entry point only enqueues work on `stream` and returns
+ *     without synchronising, except aug_read_device_status and aug_autotune.
+ *   - Argument errors found on the host are returned synchronously; errors
+ *     found in device descriptors are written to the workspace status word
+ *     (read it with aug_read_device_status); the offending volume is skipped.
+ *   - Limits: every dimension in [1, 8192]; every volume below 2^31 voxels;
+ *     |T[r][c]| <= 64 for c < 3 and |T[r][3]| <= 2^20; 1 <= n_vols <= 65535.
+ */
+#ifndef AUGWARP_H
+#define AUGWARP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Binary-compatible with cudaStream_t; NULL selects the legacy default stream. */
+typedef struct CUstream_st* aug_stream_t;
+
+typedef enum {
+  AUG_OK = 0,
+  AUG_ERR_INVALID_ARG = 1, /* a host argument is out of range / NULL           */
+  AUG_ERR_CUDA = 2,        /* a CUDA runtime call or kernel launch failed       */
+  AUG_ERR_WORKSPACE = 3,   /* workspace NULL, misaligned or too small           */
+  AUG_ERR_DESCRIPTOR = 4,  /* (device status) a volume descriptor is invalid    */
+  AUG_ERR_UNSUPPORTED = 5  /* valid request outside what this build implements  */
+} aug_status;
+
+typedef enum { AUG_F32 = 0, AUG_I16 = 1 } aug_dtype;
+
+/*
+ * One volume of a batch.  Arrays of these live in DEVICE memory, so a CUDA
+ * graph captured once can be replayed with new parameters written into the
+ * same descriptor buffer.  144 bytes, 16-byte aligned.
+ */
+typedef struct __attribute__((aligned(16))) {
+  const void* image;       /* [in_nz][in_ny][in_nx] of image_dtype                */
+  const uint8_t* label;    /* same shape, or NULL (no label warp)                 */
+  float* out_image;        /* [out_nz][out_ny][out_nx] float32, or NULL           */
+  uint8_t* out_label;      /* same shape as out_image; NULL, or label != NULL     */
+  int32_t in_nx, in_ny, in_nz;
+  int32_t image_dtype;     /* aug_dtype                                           */
+  int32_t out_nx, out_ny, out_nz;
+  int32_t fill_label;      /* 0..255                                              */
+  float affine[12];        /* T, row-major 3x4, output index -> input coordinate  */
+  float photo_a, photo_b;  /* intensity affine y = a v + b                        */
+  float noise_sigma;       /* standard deviation of the additive noise (>= 0)    */
+  float fill_image;        /* value of every input tap outside the volume         */
+  uint32_t noise_id;       /* third Philox counter word (usually the batch index) */
+  uint32_t reserved[3];    /* must be zero                                        */
+} aug_volume_desc;
+
+/* ---- workspace ----------------------------------------------------------
+ * Device scratch every batched entry point needs: a status word and
+ * per-block partial sums.  Allocate at least aug_workspace_size() bytes,
+ * 256-byte aligned, zero-filled once before first use (the status word then
+ * stays zero until a device-side error is recorded).  One workspace may be
+ * reused by consecutive calls on one stream; concurrent calls need separate
+ * workspaces.  Returns 0 if the arguments are out of range or no CUDA device
+ * is present.  Host function; queries the current device once. */
+size_t aug_workspace_size(int n_vols, int n_classes);
+
+/* Reads (and, if clear != 0, resets) the device status word of a workspace.
+ * Synchronises `stream`.  Returns the first device-side error recorded since
+ * the last clear (AUG_OK if none); *bad_volume (may be NULL) receives the
+ * index of the offending volume or -1. */
+aug_status aug_read_device_status(void* d_workspace, aug_stream_t stream, int clear,
+                                  int* bad_volume);
+
+/* ---- forward warp (Sec. 4) -------------------------------------------------
+ * Augments n_vols volumes of arbitrary, unequal sizes in ONE persistent launch.
+ * For each descriptor: out_image (if not NULL) receives the trilinear image
+ * sample passed through the intensity affine and the additive noise, and
+ * out_label (if not NULL) the nearest-neighbour label.  Output voxels whose
+ * every tap lies outside the input read the fill values.
+ *
+ * Noise: for output voxel (i, j, k), quad index Q = ((k >> 2) * out_ny + j)
+ * * out_nx + i and lane l = k & 3.  Philox4x32-10 with key (lo32(seed),
+ * hi32(seed)) and counter (lo32(Q), hi32(Q), noise_id, 0) yields r0..r3;
+ * lanes 0-1 use (ra, rb) = (r0, r1), lanes 2-3 (r2, r3);
+ * u1 = ((ra >> 8) + 1) 2^-24, u2 = (rb >> 8) 2^-24, R = sqrt(-2 ln u1);
+ * n = R cos(2 pi u2) for even l, R sin(2 pi u2) for odd l.  noise_sigma == 0
+ * adds exactly nothing.
+ *
+ * d_descs: device array of n_vols descriptors.  d_workspace: see above.
+ * Errors: AUG_ERR_INVALID_ARG (n_vols out of range, d_descs NULL),
+ * AUG_ERR_WORKSPACE, AUG_ERR_CUDA (launch failure). */
+aug_status aug_warp_fwd(const aug_volume_desc* d_descs, int n_vols, uint64_t seed,
+                        void* d_workspace, size_t workspace_bytes, aug_stream_t stream);
+
+/* The same computation for ONE volume in its own non-persistent launch (one
+ * CTA per output tile), with the descriptor passed by value from HOST memory:
+ * the plain one-volume-per-launch form, kept as the comparison point for the
+ * batched launch.  h_desc: host pointer.  Descriptor errors are returned
+ * synchronously as AUG_ERR_DESCRIPTOR. */
+aug_status aug_warp_fwd_volume(const aug_volume_desc* h_desc, uint64_t seed,
+                               aug_stream_t stream);
+
+/* ---- adjoint of the image warp ---------------------------------------------
+ * For upstream gradients g_b (shape of out_image of volume b, float32):
+ *   grad_in_b[n]    = sum_o photo_a g_b(o) w_{n}(o)       over in-volume taps,
+ *   grad_affine_b[r][c] = sum_o photo_a g_b(o) dv/ds_r(o) obar_c(o),
+ * with w the trilinear weights, obar = (i, j, k, 1) and dv/ds_r the derivative
+ * of the trilinear sample along axis r (fill taps included; the cell is the
+ * one chosen by floor(s), i.e. right derivatives at integer coordinates).
+ * The noise and photo_b do not depend on the input or on T.
+ *
+ * d_grad_out: device array of n_vols device pointers (output shape).
+ * d_grad_in:  device array of n_vols device pointers (input shape, float32
+ *             images only), or NULL to skip; overwritten (the library zeroes
+ *             them first).  Accumulated with atomics: run-to-run rounding
+ *             order may differ.
+ * d_grad_affine: [n_vols][12] float32, or NULL to skip; overwritten;
+ *             reduced in a fixed order (bitwise reproducible).
+ * Errors as aug_warp_fwd; an int16 volume with d_grad_in != NULL is a
+ * descriptor error. */
+aug_status aug_warp_bwd(const aug_volume_desc* d_descs, int n_vols,
+                        const float* const* d_grad_out, float* const* d_grad_in,
+                        float* d_grad_affine, void* d_workspace, size_t workspace_bytes,
+                        aug_stream_t stream);
+
+/* ---- fused label warp + soft IOU loss (Sec. 5.C) ----------------------------
+ * For each volume b and class c in 0..n_classes-1 (labels outside 0..C-1 belong
+ * to no class), with y_k = [nearest warped label at output voxel k == c]:
+ *   I = sum_k p_k y_k, P = sum_k p_k, Y = sum_k y_k, U = P + Y - I,
+ *   L_bc = 1 - I / U  (0 where U == 0),
+ *   loss[b] = mean_c L_bc,
+ *   grad_p[b][c][k] = d(mean_b loss[b]) / d p = (1 / (B C)) (y_k ? -1/U : I/U^2)
+ * (0 where U == 0).  The warped labels are recomputed in registers by both
+ * passes and never written to memory.
+ *
+ * d_p: float32, volumes packed consecutively, volume b as [C][out_nz][out_ny]
+ * [out_nx] at offset C * sum_{b'<b} nvox_{b'}.  d_grad_p: same layout, or NULL
+ * for the loss only.  d_loss: [n_vols] float32.  Uses each descriptor's label,
+ * affine, out dims and fill_label; the image fields are ignored.
+ * 1 <= n_classes <= 8, else AUG_ERR_UNSUPPORTED. */
+aug_status iou_loss_fwd_bwd(const aug_volume_desc* d_descs, int n_vols, const float* d_p,
+                            int n_classes, float* d_loss, float* d_grad_p, void* d_workspace,
+                            size_t workspace_bytes, aug_stream_t stream);
+
+/* ---- kernel variants and autotuning -----------------------------------------
+ * op: 0 = aug_warp_fwd, 1 = aug_warp_bwd, 2 = iou_loss_fwd_bwd.
+ * Variants differ in tile shape (warps per CTA along y, z-run per thread);
+ * all compute the same result.  Settings are process-wide host state. */
+int aug_num_variants(int op);
+const char* aug_variant_name(int op, int variant);
+/* variant -1 restores the built-in default. */
+aug_status aug_set_variant(int op, int variant);
+int aug_get_variant(int op);
+
+/* Times every variant of `op` on the given batch (reps launches each, after
+ * one warm-up, CUDA events on `stream`), selects the fastest with
+ * aug_set_variant and returns it in *best (may be NULL) with its mean time in
+ * *best_ms (may be NULL).  Synchronises `stream`; must not be called while
+ * the stream is being captured.  The arguments are those of the op's entry
+ * point; unused ones may be NULL/0 (op 0 uses d_descs, n_vols, seed; op 1
+ * adds d_grad_out, d_grad_in, d_grad_affine; op 2 adds d_p, n_classes, d_loss,
+ * d_grad_p).  The outputs of the op are overwritten. */
+aug_status aug_autotune(int op, const aug_volume_desc* d_descs, int n_vols, uint64_t seed,
+                        const float* const* d_grad_out, float* const* d_grad_in,
+                        float* d_grad_affine, const float* d_p, int n_classes, float* d_loss,
+                        float* d_grad_p, void* d_workspace, size_t workspace_bytes,
+                        aug_stream_t stream, int reps, int* best, float* best_ms);
+
+/* ---- diagnostics -------------------------------------------------------------
+ * Philox4x32-10 words computed by the device generator the warp uses:
+ * d_out[4m..4m+3] = Philox4x32-10(counter = d_ctr[4m..4m+3], key = (lo32(seed),
+ * hi32(seed))), m < n.  For bit-exact comparison with other implementations. */
+aug_status aug_philox4x32_10(const uint32_t* d_ctr, int64_t n, uint64_t seed,
+                             uint32_t* d_out, aug_stream_t stream);
+
+/* Human-readable name of a status code.  Host function, never NULL. */
+const char* aug_status_string(int status);
+
+/* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
+int aug_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* AUGWARP_H */

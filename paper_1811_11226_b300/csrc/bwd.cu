@@ -1,0 +1,264 @@
+// Adjoint of the image warp (the backward pass of the augmentation, which the
+// paper does not have; it lets gradients reach the input volume and the 12
+// affine parameters).
+//
+// For out(o) = a * sum_d w_d(o) V(f(o) + d) + b + sigma n(o):
+//   grad_in[n]   += a g(o) w_d(o)                  (scatter, in-volume taps)
+//   dv/ds_x       = lerp_z(lerp_y(V1yz - V0yz))     (x-differences of the cell)
+//   dv/ds_y       = lerp_z(c1z - c0z),  dv/ds_z = c1 - c0   (from the lerps)
+//   grad_T[r][c] += a g(o) dv/ds_r obar_c,  obar = (i, j, k, 1).
+//
+// grad_in is accumulated with float atomics straight into the caller's
+// buffer (zeroed first by k_zero_grad_in).  grad_T: per thread, S_r = sum
+// a g dv_r and K_r = sum a g dv_r k over its z-run (i, j fixed); the tile's
+// 12 sums (i S_r, j S_r, K_r, S_r) are warp-reduced, block-reduced in a
+// fixed order, accumulated per CTA and volume in double, written to
+// workspace partials [CTA][volume][12], and summed over CTAs in a fixed order
+// by k_bwd_finalize: bitwise reproducible.
+#include "kernels.h"
+#include "sample.cuh"
+
+namespace augk {
+
+template <typename TIn, int MODE, bool GIN, bool GT>
+__device__ __forceinline__ void bwd_run(const VolConst& vc, const TileCoord& tc, long long sx,
+                                        long long sy, long long sz,
+                                        const float* __restrict__ g, float* __restrict__ gin,
+                                        float acc[6]) {
+  const TIn* __restrict__ img = (const TIn*)vc.image;
+  const long long dx = vc.tq[0][2], dy = vc.tq[1][2], dz = vc.tq[2][2];
+  const int nx = vc.nx, ny = vc.ny, nz = vc.nz, nxy = nx * ny;
+  const int plane = vc.onx * vc.ony;
+  const float a = vc.a, fill = vc.fill;
+  int o = (tc.k0 * vc.ony + tc.jc) * vc.onx + tc.ic;
+#pragma unroll 4
+  for (int k = tc.k0; k < tc.k1; ++k) {
+    const float ga = tc.valid ? a * __ldcs(g + o) : 0.0f;
+    Taps t;
+    load_taps<TIn, MODE>(img, sx, sy, sz, nx, ny, nz, fill, t);
+    if (GIN && tc.valid) {
+      const float wx1 = t.tx, wx0 = 1.0f - t.tx, wy1 = t.ty, wy0 = 1.0f - t.ty;
+      const float wz1 = t.tz, wz0 = 1.0f - t.tz;
+      const float g00 = ga * wy0 * wz0, g10 = ga * wy1 * wz0;
+      const float g01 = ga * wy0 * wz1, g11 = ga * wy1 * wz1;
+      if (MODE == MODE_INTERIOR) {
+        float* p = gin + ((t.fz * ny + t.fy) * nx + t.fx);
+        atomicAdd(p, g00 * wx0);
+        atomicAdd(p + 1, g00 * wx1);
+        atomicAdd(p + nx, g10 * wx0);
+        atomicAdd(p + nx + 1, g10 * wx1);
+        atomicAdd(p + nxy, g01 * wx0);
+        atomicAdd(p + nxy + 1, g01 * wx1);
+        atomicAdd(p + nxy + nx, g11 * wx0);
+        atomicAdd(p + nxy + nx + 1, g11 * wx1);
+      } else {
+        const bool x0 = (unsigned)t.fx < (unsigned)nx, x1 = (unsigned)(t.fx + 1) < (unsigned)nx;
+        const bool y0 = (unsigned)t.fy < (unsigned)ny, y1 = (unsigned)(t.fy + 1) < (unsigned)ny;
+        const bool z0 = (unsigned)t.fz < (unsigned)nz, z1 = (unsigned)(t.fz + 1) < (unsigned)nz;
+        const unsigned base = ((unsigned)t.fz * (unsigned)ny + (unsigned)t.fy) * (unsigned)nx +
+                              (unsigned)t.fx;
+        const unsigned ux = (unsigned)nx, uxy = (unsigned)nxy;
+        if (x0 && y0 && z0) atomicAdd(gin + base, g00 * wx0);
+        if (x1 && y0 && z0) atomicAdd(gin + (base + 1u), g00 * wx1);
+        if (x0 && y1 && z0) atomicAdd(gin + (base + ux), g10 * wx0);
+        if (x1 && y1 && z0) atomicAdd(gin + (base + ux + 1u), g10 * wx1);
+        if (x0 && y0 && z1) atomicAdd(gin + (base + uxy), g01 * wx0);
+        if (x1 && y0 && z1) atomicAdd(gin + (base + uxy + 1u), g01 * wx1);
+        if (x0 && y1 && z1) atomicAdd(gin + (base + uxy + ux), g11 * wx0);
+        if (x1 && y1 && z1) atomicAdd(gin + (base + uxy + ux + 1u), g11 * wx1);
+      }
+    }
+    if (GT) {
+      float c00, c10, c01, c11, c0, c1;
+      trilerp(t, c00, c10, c01, c11, c0, c1);
+      const float e0 = fmaf(t.ty, (t.v110 - t.v010) - (t.v100 - t.v000), t.v100 - t.v000);
+      const float e1 = fmaf(t.ty, (t.v111 - t.v011) - (t.v101 - t.v001), t.v101 - t.v001);
+      const float dvx = fmaf(t.tz, e1 - e0, e0);
+      const float dvy = fmaf(t.tz, (c11 - c01) - (c10 - c00), c10 - c00);
+      const float dvz = c1 - c0;
+      const float kf = (float)k;
+      acc[0] = fmaf(ga, dvx, acc[0]);
+      acc[1] = fmaf(ga, dvy, acc[1]);
+      acc[2] = fmaf(ga, dvz, acc[2]);
+      acc[3] = fmaf(ga * dvx, kf, acc[3]);
+      acc[4] = fmaf(ga * dvy, kf, acc[4]);
+      acc[5] = fmaf(ga * dvz, kf, acc[5]);
+    }
+    sx += dx;
+    sy += dy;
+    sz += dz;
+    o += plane;
+  }
+}
+
+template <int NW>
+struct BwdShared {
+  VolConst vc;
+  float red[NW][12];
+  double acc[12];
+};
+
+template <typename TIn, int NW, int QZ, bool GIN, bool GT>
+__device__ __forceinline__ void bwd_tile(BwdShared<NW>& sh, int t, const float* g, float* gin) {
+  const VolConst& vc = sh.vc;
+  const TileCoord tc = tile_coord<NW, QZ>(t, vc.onx, vc.ony, vc.onz);
+  long long s[3], ds[3];
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    s[r] = coord_q40(vc.tq[r], tc.ic, tc.jc, tc.k0);
+    ds[r] = vc.tq[r][2];
+  }
+  float acc[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+  const int mode =
+      warp_mode(classify_run<true>(s, ds, tc.k1 - 1 - tc.k0, vc.nx, vc.ny, vc.nz));
+  // Exterior cells have all taps equal to the fill value: no gradient at all.
+  if (mode == MODE_INTERIOR)
+    bwd_run<TIn, MODE_INTERIOR, GIN, GT>(vc, tc, s[0], s[1], s[2], g, gin, acc);
+  else if (mode == MODE_GENERAL)
+    bwd_run<TIn, MODE_GENERAL, GIN, GT>(vc, tc, s[0], s[1], s[2], g, gin, acc);
+  if (GT) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const float fi = (float)tc.ic, fj = (float)tc.jc;
+    float v[12];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      v[4 * r + 0] = fi * acc[r];
+      v[4 * r + 1] = fj * acc[r];
+      v[4 * r + 2] = acc[3 + r];
+      v[4 * r + 3] = acc[r];
+    }
+#pragma unroll
+    for (int m = 0; m < 12; ++m) {
+      const float w = warp_sum(v[m]);
+      if (lane == 0) sh.red[warp][m] = w;
+    }
+    __syncthreads();
+    if (threadIdx.x < 12) {
+      double tot = 0.0;
+#pragma unroll
+      for (int w = 0; w < NW; ++w) tot += (double)sh.red[w][threadIdx.x];
+      sh.acc[threadIdx.x] += tot;
+    }
+    __syncthreads();
+  }
+}
+
+template <int NW, int QZ, bool GIN, bool GT>
+__global__ void __launch_bounds__(NW * 32)
+    k_bwd_batched(const aug_volume_desc* __restrict__ descs, int n_vols,
+                  const float* const* gout, float* const* gin, double* partials, WsHeader* ws) {
+  __shared__ BwdShared<NW> sh;
+  long long base = 0;
+  for (int v = 0; v < n_vols; ++v) {
+    __syncthreads();
+    stage_volume(descs + v, v, sh.vc, ws, true, GIN);
+    if (threadIdx.x < 12) sh.acc[threadIdx.x] = 0.0;
+    __syncthreads();
+    const float* g = gout[v];
+    float* gi = GIN ? gin[v] : nullptr;
+    const bool ok = sh.vc.ok && g != nullptr && (!GIN || gi != nullptr);
+    if (!ok && sh.vc.ok && blockIdx.x == 0 && threadIdx.x == 0)
+      record_error(ws, AUG_ERR_DESCRIPTOR, v);
+    const int nt = sh.vc.ok ? tiles_in<NW, QZ>(sh.vc.onx, sh.vc.ony, sh.vc.onz) : 0;
+    if (ok) {
+      for (long long t = first_tile(base); t < nt; t += gridDim.x) {
+        if (sh.vc.dtype == AUG_I16)
+          bwd_tile<int16_t, NW, QZ, GIN, GT>(sh, (int)t, g, gi);
+        else
+          bwd_tile<float, NW, QZ, GIN, GT>(sh, (int)t, g, gi);
+      }
+    }
+    if (GT && threadIdx.x < 12)
+      partials[((size_t)blockIdx.x * n_vols + v) * 12 + threadIdx.x] = sh.acc[threadIdx.x];
+    base += nt;
+  }
+}
+
+// Zero every grad_in volume (float32 input shape) before the scatter.
+__global__ void k_zero_grad_in(const aug_volume_desc* __restrict__ descs, int n_vols,
+                               float* const* gin) {
+  for (int v = 0; v < n_vols; ++v) {
+    float* p = gin[v];
+    const aug_volume_desc& d = descs[v];
+    if (p == nullptr || d.in_nx < 1 || d.in_ny < 1 || d.in_nz < 1 || d.in_nx > MAX_DIM ||
+        d.in_ny > MAX_DIM || d.in_nz > MAX_DIM)
+      continue;
+    const long long n = (long long)d.in_nx * d.in_ny * d.in_nz;
+    if (n >= (1LL << 31)) continue;
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long t0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if ((((uintptr_t)p) & 15) == 0) {
+      float4* p4 = reinterpret_cast<float4*>(p);
+      const long long n4 = n >> 2;
+      for (long long m = t0; m < n4; m += stride) p4[m] = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (long long m = (n4 << 2) + t0; m < n; m += stride) p[m] = 0.0f;
+    } else {
+      for (long long m = t0; m < n; m += stride) p[m] = 0.0f;
+    }
+  }
+}
+
+// grad_affine[v][m] = sum over CTAs of partials[cta][v][m], fixed order.
+__global__ void k_bwd_finalize(const double* __restrict__ partials, int n_ctas, int n_vols,
+                               float* grad_affine) {
+  const int v = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int m = warp; m < 12; m += blockDim.x >> 5) {
+    double s = 0.0;
+    for (int c = lane; c < n_ctas; c += 32) s += partials[((size_t)c * n_vols + v) * 12 + m];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(FULL_MASK, s, off);
+    if (lane == 0) grad_affine[(size_t)v * 12 + m] = (float)s;
+  }
+}
+
+// ---- host launchers ------------------------------------------------------------
+namespace {
+struct BwdVariant {
+  int nw, qz;
+  const void* k[4];  // [GIN*2 + GT]
+};
+#define BWD_V(NW, QZ)                                                               \
+  {                                                                                 \
+    NW, QZ,                                                                         \
+        {(const void*)k_bwd_batched<NW, QZ, false, false>,                          \
+         (const void*)k_bwd_batched<NW, QZ, false, true>,                           \
+         (const void*)k_bwd_batched<NW, QZ, true, false>,                           \
+         (const void*)k_bwd_batched<NW, QZ, true, true> }                           \
+  }
+const BwdVariant kBwd[] = {BWD_V(8, 4), BWD_V(4, 4), BWD_V(8, 2), BWD_V(8, 8), BWD_V(4, 8)};
+#undef BWD_V
+const char* kBwdNames[] = {"tile32x8x16", "tile32x4x16", "tile32x8x8", "tile32x8x32",
+                           "tile32x4x32"};
+}  // namespace
+
+int bwd_num_variants() { return (int)(sizeof(kBwd) / sizeof(kBwd[0])); }
+const char* bwd_variant_name(int v) { return kBwdNames[v]; }
+
+cudaError_t launch_bwd(int variant, const aug_volume_desc* d, int n, const float* const* gout,
+                       float* const* gin, float* gaff, double* partials, WsHeader* ws,
+                       cudaStream_t st) {
+  const BwdVariant& bv = kBwd[variant];
+  const bool want_gin = gin != nullptr, want_gt = gaff != nullptr;
+  if (!want_gin && !want_gt) return cudaSuccess;
+  cudaError_t e;
+  if (want_gin) {
+    const int zgrid = persistent_grid((const void*)k_zero_grad_in, 256, 0);
+    if (zgrid <= 0) return cudaErrorInvalidConfiguration;
+    k_zero_grad_in<<<zgrid, 256, 0, st>>>(d, n, gin);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  const void* kern = bv.k[(want_gin ? 2 : 0) + (want_gt ? 1 : 0)];
+  const int block = bv.nw * 32;
+  const int grid = persistent_grid(kern, block, 0);
+  if (grid <= 0) return cudaErrorInvalidConfiguration;
+  void* args[] = {(void*)&d, (void*)&n, (void*)&gout, (void*)&gin, (void*)&partials, (void*)&ws};
+  if ((e = cudaLaunchKernel(kern, dim3(grid), dim3(block), args, 0, st)) != cudaSuccess) return e;
+  if (want_gt) {
+    k_bwd_finalize<<<n, 384, 0, st>>>(partials, grid, n, gaff);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace augk

@@ -1,0 +1,182 @@
+// Device helpers shared by the augmentation kernels (sm_103a).
+//
+// Coordinates: s = A o + b (Sec. 4) is evaluated in signed 64-bit fixed point
+// with 40 fractional bits ("Q.40").  Every float32 affine entry with
+// |T| >= 2^-17 is exact in Q.40 and integer output indices are exact, so the
+// coordinate equals the real-number value A o + b exactly; floor/round
+// decisions (cell choice, nearest label) are therefore exact, and only the
+// interpolation weight is rounded (to 24 bits).  Float32 coordinates would be
+// off by up to ~1.5e-5 voxel at |s| ~ 200, i.e. ~0.02 HU at a 1000 HU edge.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "augwarp.h"
+
+namespace augk {
+
+constexpr unsigned FULL_MASK = 0xffffffffu;
+constexpr int MAX_DIM = 8192;
+
+// Workspace layout: a 256-byte header (status words), then op scratch.
+struct WsHeader {
+  int status;      // first device-side error (aug_status), 0 if none
+  int bad_volume;  // volume index of that error
+  int pad[62];
+};
+static_assert(sizeof(WsHeader) == 256, "header size");
+
+__device__ __forceinline__ void record_error(WsHeader* ws, int code, int vol) {
+  if (ws == nullptr) return;
+  if (atomicCAS(&ws->status, 0, code) == 0) ws->bad_volume = vol;
+}
+
+// Per-volume constants staged in shared memory by each CTA.
+struct VolConst {
+  long long tq[3][4];  // affine in Q.40
+  const void* image;
+  const uint8_t* label;
+  float* out_image;
+  uint8_t* out_label;
+  int nx, ny, nz, dtype;
+  int onx, ony, onz, fill_label;
+  float a, b, sigma, fill;
+  unsigned noise_id;
+  int ok;
+};
+
+// Threads of the CTA cooperate; the caller must __syncthreads() afterwards.
+// Validates the descriptor; ok = 0 marks it invalid (the error is recorded by
+// CTA 0 only).  need_image: out_image requires an image of a known dtype;
+// f32_only: the image must be float32.
+__device__ inline void stage_volume(const aug_volume_desc* __restrict__ d, int v, VolConst& vc,
+                                    WsHeader* ws, bool need_image, bool f32_only) {
+  if (threadIdx.x < 12) {
+    const int r = threadIdx.x >> 2, c = threadIdx.x & 3;
+    const float t = d->affine[threadIdx.x];
+    const float lim = (c < 3) ? 64.0f : 1048576.0f;
+    long long q = 0;
+    if (isfinite(t) && fabsf(t) <= lim) q = __double2ll_rn((double)t * 1099511627776.0);
+    vc.tq[r][c] = q;
+  }
+  if (threadIdx.x == 0) {
+    vc.image = d->image;
+    vc.label = d->label;
+    vc.out_image = d->out_image;
+    vc.out_label = d->out_label;
+    vc.nx = d->in_nx;
+    vc.ny = d->in_ny;
+    vc.nz = d->in_nz;
+    vc.dtype = d->image_dtype;
+    vc.onx = d->out_nx;
+    vc.ony = d->out_ny;
+    vc.onz = d->out_nz;
+    vc.fill_label = d->fill_label;
+    vc.a = d->photo_a;
+    vc.b = d->photo_b;
+    vc.sigma = d->noise_sigma;
+    vc.fill = d->fill_image;
+    vc.noise_id = d->noise_id;
+    bool ok = true;
+    ok &= vc.nx >= 1 && vc.ny >= 1 && vc.nz >= 1 && vc.nx <= MAX_DIM && vc.ny <= MAX_DIM &&
+          vc.nz <= MAX_DIM;
+    ok &= vc.onx >= 1 && vc.ony >= 1 && vc.onz >= 1 && vc.onx <= MAX_DIM &&
+          vc.ony <= MAX_DIM && vc.onz <= MAX_DIM;
+    ok &= (long long)vc.nx * vc.ny * vc.nz < (1LL << 31);
+    ok &= (long long)vc.onx * vc.ony * vc.onz < (1LL << 31);
+    ok &= vc.fill_label >= 0 && vc.fill_label <= 255;
+    for (int m = 0; m < 12; ++m) {
+      const float t = d->affine[m];
+      ok &= isfinite(t) && fabsf(t) <= (((m & 3) < 3) ? 64.0f : 1048576.0f);
+    }
+    ok &= isfinite(vc.a) && isfinite(vc.b) && isfinite(vc.sigma) && vc.sigma >= 0.0f &&
+          isfinite(vc.fill);
+    ok &= d->reserved[0] == 0u && d->reserved[1] == 0u && d->reserved[2] == 0u;
+    if (need_image) {
+      ok &= vc.image != nullptr && (vc.dtype == AUG_F32 || vc.dtype == AUG_I16);
+      if (f32_only) ok &= vc.dtype == AUG_F32;
+    }
+    ok &= !(vc.out_label != nullptr && vc.label == nullptr);
+    vc.ok = ok ? 1 : 0;
+    if (!ok && blockIdx.x == 0) record_error(ws, AUG_ERR_DESCRIPTOR, v);
+  }
+}
+
+// ---- Q.40 coordinate helpers ------------------------------------------------
+__device__ __forceinline__ int q40_hi(long long s) { return (int)(s >> 32); }
+// floor(s)
+__device__ __forceinline__ int q40_floor(long long s) { return q40_hi(s) >> 8; }
+// floor(s + 1/2): adding 2^39 only touches the high word.
+__device__ __forceinline__ int q40_round(long long s) { return (q40_hi(s) + 128) >> 8; }
+// s - floor(s), truncated to 24 bits (error < 2^-24).
+__device__ __forceinline__ float q40_frac(long long s) {
+  const unsigned m = (unsigned)((unsigned long long)s >> 16) & 0xFFFFFFu;
+  return __uint2float_rn(m) * 5.9604644775390625e-8f;
+}
+
+template <typename T>
+__device__ __forceinline__ float ld_val(const T* p);
+template <>
+__device__ __forceinline__ float ld_val<float>(const float* p) {
+  return __ldg(p);
+}
+template <>
+__device__ __forceinline__ float ld_val<int16_t>(const int16_t* p) {
+  return (float)__ldg(p);
+}
+
+// ---- Philox4x32-10 (Salmon et al., SC'11) -----------------------------------
+// Round: (hi0, lo0) = M0 * c0, (hi1, lo1) = M1 * c2;
+//        c <- (hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0); key += Weyl constants.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, unsigned k0, unsigned k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r > 0) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const unsigned lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
+    const unsigned lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
+    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+  }
+  return c;
+}
+
+// Box-Muller on one pair of words: (R cos 2 pi u2, R sin 2 pi u2).
+__device__ __forceinline__ float2 box_muller(unsigned ra, unsigned rb) {
+  const float u1 = (float)((ra >> 8) + 1u) * 5.9604644775390625e-8f;  // (0, 1], exact
+  const float u2 = (float)(rb >> 8) * 5.9604644775390625e-8f;          // [0, 1), exact
+  const float r = sqrtf(-2.0f * logf(u1));
+  float s, c;
+  sincospif(2.0f * u2, &s, &c);
+  return make_float2(r * c, r * s);
+}
+
+// Four normals of one quad (lanes 0..3).
+__device__ __forceinline__ void quad_normals(unsigned long long quad, unsigned noise_id,
+                                             unsigned k0, unsigned k1, float z[4]) {
+  const uint4 r = philox4x32_10(
+      make_uint4((unsigned)quad, (unsigned)(quad >> 32), noise_id, 0u), k0, k1);
+  const float2 p = box_muller(r.x, r.y), q = box_muller(r.z, r.w);
+  z[0] = p.x;
+  z[1] = p.y;
+  z[2] = q.x;
+  z[3] = q.y;
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL_MASK, v, o);
+  return v;
+}
+
+// Static round-robin tile schedule over the concatenated tile lists of all
+// volumes: CTA b of G takes global tiles b, b + G, ...  For a volume whose
+// tiles start at global index `base`, returns the first local tile of this CTA.
+__device__ __forceinline__ long long first_tile(long long base) {
+  const long long G = gridDim.x;
+  return ((long long)blockIdx.x - base % G + G) % G;
+}
+
+}  // namespace augk

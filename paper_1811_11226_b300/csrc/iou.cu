@@ -1,0 +1,232 @@
+// Fused nearest-label warp + soft IOU loss, forward and backward (Sec. 5.C).
+//
+//   pass 1 (k_iou_pass<SUMS=true>): per output voxel, the warped label y is
+//       computed in registers (exact Q.40 coordinate, floor(s + 1/2)) and the
+//       class probabilities p[c] are streamed once; per class the sums
+//       I = sum p [y == c], P = sum p, Y = sum [y == c] are reduced per tile
+//       (warp shuffles, then a fixed-order block sum in double) and per CTA,
+//       and written to workspace partials [CTA][volume][3C].
+//   finalize (k_iou_finalize): one CTA per volume sums the partials over CTAs
+//       in a fixed order, writes loss[b] = mean_c (1 - I/U) and the two
+//       gradient values of each class: -s/U (voxels of the class) and
+//       s I/U^2 (other voxels), s = 1/(B C).
+//   pass 2 (k_iou_pass<SUMS=false>): recomputes the label and writes grad_p
+//       (a write-only stream; p is not re-read).
+// The warped labels never reach memory.
+#include "kernels.h"
+#include "sample.cuh"
+
+namespace augk {
+
+template <int MODE, int C, bool SUMS>
+__device__ __forceinline__ void iou_run(const VolConst& vc, const TileCoord& tc, long long sx,
+                                        long long sy, long long sz,
+                                        const float* __restrict__ p, float* __restrict__ gp,
+                                        const float2* __restrict__ cf, float acc[3 * C]) {
+  const long long dx = vc.tq[0][2], dy = vc.tq[1][2], dz = vc.tq[2][2];
+  const int plane = vc.onx * vc.ony;
+  const int nvox = plane * vc.onz;
+  int o = (tc.k0 * vc.ony + tc.jc) * vc.onx + tc.ic;
+  float2 coef[C];
+  if (!SUMS) {
+#pragma unroll
+    for (int c = 0; c < C; ++c) coef[c] = cf[c];
+  }
+#pragma unroll 4
+  for (int k = tc.k0; k < tc.k1; ++k) {
+    const int y = load_label<MODE>(vc.label, sx, sy, sz, vc.nx, vc.ny, vc.nz, vc.fill_label);
+    if (tc.valid) {
+      if (SUMS) {
+#pragma unroll
+        for (int c = 0; c < C; ++c) {
+          const float pc = __ldcs(p + (size_t)c * nvox + o);
+          const bool hit = y == c;
+          acc[3 * c + 0] += hit ? pc : 0.0f;
+          acc[3 * c + 1] += pc;
+          acc[3 * c + 2] += hit ? 1.0f : 0.0f;
+        }
+      } else {
+#pragma unroll
+        for (int c = 0; c < C; ++c)
+          __stcs(gp + (size_t)c * nvox + o, y == c ? coef[c].y : coef[c].x);
+      }
+    }
+    sx += dx;
+    sy += dy;
+    sz += dz;
+    o += plane;
+  }
+}
+
+template <int NW, int C>
+struct IouShared {
+  VolConst vc;
+  float red[NW][3 * C];
+  double acc[3 * C];
+};
+
+template <int NW, int QZ, int C, bool SUMS>
+__global__ void __launch_bounds__(NW * 32)
+    k_iou_pass(const aug_volume_desc* __restrict__ descs, int n_vols,
+               const float* __restrict__ p, float* __restrict__ gp,
+               const float2* __restrict__ coefs, double* partials, WsHeader* ws) {
+  __shared__ IouShared<NW, C> sh;
+  long long base = 0;
+  size_t poff = 0;  // offset of this volume's [C][nvox] block
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int v = 0; v < n_vols; ++v) {
+    __syncthreads();
+    stage_volume(descs + v, v, sh.vc, SUMS ? ws : nullptr, false, false);
+    if (SUMS && threadIdx.x < 3 * C) sh.acc[threadIdx.x] = 0.0;
+    __syncthreads();
+    const VolConst& vc = sh.vc;
+    const bool ok = vc.ok && vc.label != nullptr;
+    if (SUMS && vc.ok && vc.label == nullptr && blockIdx.x == 0 && threadIdx.x == 0)
+      record_error(ws, AUG_ERR_DESCRIPTOR, v);
+    const int nt = vc.ok ? tiles_in<NW, QZ>(vc.onx, vc.ony, vc.onz) : 0;
+    const size_t nvox = vc.ok ? (size_t)vc.onx * vc.ony * vc.onz : 0;
+    if (ok) {
+      for (long long t = first_tile(base); t < nt; t += gridDim.x) {
+        const TileCoord tc = tile_coord<NW, QZ>((int)t, vc.onx, vc.ony, vc.onz);
+        long long s[3], ds[3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r) {
+          s[r] = coord_q40(vc.tq[r], tc.ic, tc.jc, tc.k0);
+          ds[r] = vc.tq[r][2];
+        }
+        float acc[3 * C];
+#pragma unroll
+        for (int m = 0; m < 3 * C; ++m) acc[m] = 0.0f;
+        const int mode =
+            warp_mode(classify_run<false>(s, ds, tc.k1 - 1 - tc.k0, vc.nx, vc.ny, vc.nz));
+        const float* pv = p + poff;
+        float* gv = SUMS ? nullptr : gp + poff;
+        const float2* cf = SUMS ? nullptr : coefs + (size_t)v * C;
+        if (mode == MODE_INTERIOR)
+          iou_run<MODE_INTERIOR, C, SUMS>(vc, tc, s[0], s[1], s[2], pv, gv, cf, acc);
+        else if (mode == MODE_EXTERIOR)
+          iou_run<MODE_EXTERIOR, C, SUMS>(vc, tc, s[0], s[1], s[2], pv, gv, cf, acc);
+        else
+          iou_run<MODE_GENERAL, C, SUMS>(vc, tc, s[0], s[1], s[2], pv, gv, cf, acc);
+        if (SUMS) {
+#pragma unroll
+          for (int m = 0; m < 3 * C; ++m) {
+            const float w = warp_sum(acc[m]);
+            if (lane == 0) sh.red[warp][m] = w;
+          }
+          __syncthreads();
+          if (threadIdx.x < 3 * C) {
+            double tot = 0.0;
+#pragma unroll
+            for (int w = 0; w < NW; ++w) tot += (double)sh.red[w][threadIdx.x];
+            sh.acc[threadIdx.x] += tot;
+          }
+          __syncthreads();
+        }
+      }
+    }
+    if (SUMS && threadIdx.x < 3 * C)
+      partials[((size_t)blockIdx.x * n_vols + v) * (3 * C) + threadIdx.x] = sh.acc[threadIdx.x];
+    base += nt;
+    poff += (size_t)C * nvox;
+  }
+}
+
+// One CTA per volume: loss and the per-class gradient values.
+template <int C>
+__global__ void k_iou_finalize(const double* __restrict__ partials, int n_ctas, int n_vols,
+                               float* loss, float2* coefs) {
+  __shared__ double tot[3 * C];
+  const int v = blockIdx.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int m = warp; m < 3 * C; m += blockDim.x >> 5) {
+    double s = 0.0;
+    for (int c = lane; c < n_ctas; c += 32)
+      s += partials[((size_t)c * n_vols + v) * (3 * C) + m];
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) s += __shfl_xor_sync(FULL_MASK, s, off);
+    if (lane == 0) tot[m] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double scale = 1.0 / ((double)n_vols * (double)C);
+    double lsum = 0.0;
+    for (int c = 0; c < C; ++c) {
+      const double I = tot[3 * c], P = tot[3 * c + 1], Y = tot[3 * c + 2];
+      const double U = P + Y - I;
+      double l = 0.0, g_other = 0.0, g_class = 0.0;
+      if (U > 0.0) {
+        l = 1.0 - I / U;
+        g_other = scale * I / (U * U);
+        g_class = -scale / U;
+      }
+      lsum += l;
+      if (coefs) coefs[(size_t)v * C + c] = make_float2((float)g_other, (float)g_class);
+    }
+    loss[v] = (float)(lsum / C);
+  }
+}
+
+// ---- host launchers ----------------------------------------------------------------
+namespace {
+struct IouVariant {
+  int nw, qz;
+  const void* sums[8];
+  const void* grad[8];
+};
+#define IOU_K(NW, QZ, S)                                                          \
+  {                                                                               \
+    (const void*)k_iou_pass<NW, QZ, 1, S>, (const void*)k_iou_pass<NW, QZ, 2, S>, \
+        (const void*)k_iou_pass<NW, QZ, 3, S>, (const void*)k_iou_pass<NW, QZ, 4, S>, \
+        (const void*)k_iou_pass<NW, QZ, 5, S>, (const void*)k_iou_pass<NW, QZ, 6, S>, \
+        (const void*)k_iou_pass<NW, QZ, 7, S>, (const void*)k_iou_pass<NW, QZ, 8, S>  \
+  }
+#define IOU_V(NW, QZ) \
+  { NW, QZ, IOU_K(NW, QZ, true), IOU_K(NW, QZ, false) }
+const IouVariant kIou[] = {IOU_V(8, 4), IOU_V(4, 4), IOU_V(8, 8), IOU_V(4, 8)};
+#undef IOU_V
+#undef IOU_K
+const void* kIouFin[8] = {
+    (const void*)k_iou_finalize<1>, (const void*)k_iou_finalize<2>,
+    (const void*)k_iou_finalize<3>, (const void*)k_iou_finalize<4>,
+    (const void*)k_iou_finalize<5>, (const void*)k_iou_finalize<6>,
+    (const void*)k_iou_finalize<7>, (const void*)k_iou_finalize<8>};
+const char* kIouNames[] = {"tile32x8x16", "tile32x4x16", "tile32x8x32", "tile32x4x32"};
+}  // namespace
+
+int iou_num_variants() { return (int)(sizeof(kIou) / sizeof(kIou[0])); }
+const char* iou_variant_name(int v) { return kIouNames[v]; }
+
+cudaError_t launch_iou(int variant, const aug_volume_desc* d, int n, const float* p, int C,
+                       float* loss, float* gp, double* partials, float2* coefs, WsHeader* ws,
+                       cudaStream_t st) {
+  const IouVariant& iv = kIou[variant];
+  const int block = iv.nw * 32;
+  const void* ks = iv.sums[C - 1];
+  const int grid = persistent_grid(ks, block, 0);
+  if (grid <= 0) return cudaErrorInvalidConfiguration;
+  float* null_f = nullptr;
+  const float2* cnull = nullptr;
+  void* a1[] = {(void*)&d,     (void*)&n,        (void*)&p, (void*)&null_f,
+                (void*)&cnull, (void*)&partials, (void*)&ws};
+  cudaError_t e = cudaLaunchKernel(ks, dim3(grid), dim3(block), a1, 0, st);
+  if (e != cudaSuccess) return e;
+  float2* cf = gp ? coefs : nullptr;
+  int n_ctas = grid;
+  void* af[] = {(void*)&partials, (void*)&n_ctas, (void*)&n, (void*)&loss, (void*)&cf};
+  if ((e = cudaLaunchKernel(kIouFin[C - 1], dim3(n), dim3(256), af, 0, st)) != cudaSuccess)
+    return e;
+  if (gp) {
+    const void* kg = iv.grad[C - 1];
+    const int g2 = persistent_grid(kg, block, 0);
+    if (g2 <= 0) return cudaErrorInvalidConfiguration;
+    const float2* ccf = coefs;
+    double* pnull = nullptr;
+    void* a2[] = {(void*)&d, (void*)&n, (void*)&p, (void*)&gp, (void*)&ccf, (void*)&pnull,
+                  (void*)&ws};
+    if ((e = cudaLaunchKernel(kg, dim3(g2), dim3(block), a2, 0, st)) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace augk

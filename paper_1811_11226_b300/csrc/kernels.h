@@ -1,0 +1,40 @@
+// Internal host-side interface between the C ABI (api.cu) and the kernel
+// translation units.  Not installed; not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "augwarp.h"
+#include "common.cuh"
+
+namespace augk {
+
+// Grid of a persistent launch: (resident CTAs per SM, capped at
+// kMaxCtasPerSm) * SM count of the current device.  Cached per kernel.
+constexpr int kMaxCtasPerSm = 8;
+int persistent_grid(const void* kernel, int block, size_t smem);
+int device_sm_count();
+
+int fwd_num_variants();
+const char* fwd_variant_name(int v);
+cudaError_t launch_fwd_batched(int variant, const aug_volume_desc* d, int n, unsigned k0,
+                               unsigned k1, WsHeader* ws, cudaStream_t st);
+cudaError_t launch_fwd_volume(int variant, const aug_volume_desc& h, unsigned k0, unsigned k1,
+                              cudaStream_t st);
+
+int bwd_num_variants();
+const char* bwd_variant_name(int v);
+cudaError_t launch_bwd(int variant, const aug_volume_desc* d, int n, const float* const* gout,
+                       float* const* gin, float* gaff, double* partials, WsHeader* ws,
+                       cudaStream_t st);
+
+int iou_num_variants();
+const char* iou_variant_name(int v);
+cudaError_t launch_iou(int variant, const aug_volume_desc* d, int n, const float* p, int C,
+                       float* loss, float* gp, double* partials, float2* coefs, WsHeader* ws,
+                       cudaStream_t st);
+
+cudaError_t launch_philox(const uint32_t* ctr, long long n, unsigned k0, unsigned k1,
+                          uint32_t* out, cudaStream_t st);
+
+}  // namespace augk
