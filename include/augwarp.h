@@ -49,6 +49,12 @@
 extern "C" {
 #endif
 
+/* Every declaration below is exported from the shared library (the library
+ * is built with hidden visibility for everything else). */
+#if defined(__GNUC__)
+#pragma GCC visibility push(default)
+#endif
+
 /* Binary-compatible with cudaStream_t; NULL selects the legacy default stream. */
 typedef struct CUstream_st* aug_stream_t;
 
@@ -209,6 +215,10 @@ const char* aug_status_string(int status);
 
 /* Library version as MAJOR*10000 + MINOR*100 + PATCH. */
 int aug_version(void);
+
+#if defined(__GNUC__)
+#pragma GCC visibility pop
+#endif
 
 #ifdef __cplusplus
 }

@@ -1,0 +1,358 @@
+"""Python binding of libaugwarp.so (include/augwarp.h).
+
+Argument marshalling only: every step of the augmentation runs in the CUDA
+library.  PyTorch supplies device memory and the current stream.  The names
+mirror the C entry points (``aug_warp_fwd``, ``aug_warp_bwd``,
+``iou_loss_fwd_bwd`` ...); on top sit :class:`VolumeBatch` (descriptor
+packing) and the autograd functions :class:`AugWarp` and :class:`IouLoss`.
+
+If the compiled library is missing this module raises at import time: there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libaugwarp.so")
+
+AUG_OK, AUG_ERR_INVALID_ARG, AUG_ERR_CUDA, AUG_ERR_WORKSPACE, AUG_ERR_DESCRIPTOR, \
+    AUG_ERR_UNSUPPORTED = range(6)
+AUG_F32, AUG_I16 = 0, 1
+OP_FWD, OP_BWD, OP_IOU = 0, 1, 2
+
+# Layout of aug_volume_desc (144 bytes, 16-byte aligned).
+DESC_DTYPE = np.dtype({
+    "names": ["image", "label", "out_image", "out_label", "in_nx", "in_ny", "in_nz",
+              "image_dtype", "out_nx", "out_ny", "out_nz", "fill_label", "affine", "photo_a",
+              "photo_b", "noise_sigma", "fill_image", "noise_id", "reserved"],
+    "formats": ["<u8", "<u8", "<u8", "<u8", "<i4", "<i4", "<i4", "<i4", "<i4", "<i4", "<i4",
+                "<i4", ("<f4", (12,)), "<f4", "<f4", "<f4", "<f4", "<u4", ("<u4", (3,))],
+    "offsets": [0, 8, 16, 24, 32, 36, 40, 44, 48, 52, 56, 60, 64, 112, 116, 120, 124, 128, 132],
+    "itemsize": 144,
+})
+
+
+class AugError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        super().__init__(f"{where}: {status_string(status)} (status {status})")
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(
+            f"{LIB_PATH} is missing: build it with `python -m paper_1811_11226_b300.build` "
+            "(nvcc, sm_103a). There is no CPU fallback.")
+    L = C.CDLL(LIB_PATH)
+    vp, i32, i64, u64, sz, f32p = C.c_void_p, C.c_int, C.c_int64, C.c_uint64, C.c_size_t, \
+        C.POINTER(C.c_float)
+    L.aug_workspace_size.argtypes = [i32, i32]
+    L.aug_workspace_size.restype = sz
+    L.aug_read_device_status.argtypes = [vp, vp, i32, C.POINTER(C.c_int)]
+    L.aug_read_device_status.restype = i32
+    L.aug_warp_fwd.argtypes = [vp, i32, u64, vp, sz, vp]
+    L.aug_warp_fwd.restype = i32
+    L.aug_warp_fwd_volume.argtypes = [vp, u64, vp]
+    L.aug_warp_fwd_volume.restype = i32
+    L.aug_warp_bwd.argtypes = [vp, i32, vp, vp, vp, vp, sz, vp]
+    L.aug_warp_bwd.restype = i32
+    L.iou_loss_fwd_bwd.argtypes = [vp, i32, vp, i32, vp, vp, vp, sz, vp]
+    L.iou_loss_fwd_bwd.restype = i32
+    L.aug_num_variants.argtypes = [i32]
+    L.aug_num_variants.restype = i32
+    L.aug_variant_name.argtypes = [i32, i32]
+    L.aug_variant_name.restype = C.c_char_p
+    L.aug_set_variant.argtypes = [i32, i32]
+    L.aug_set_variant.restype = i32
+    L.aug_get_variant.argtypes = [i32]
+    L.aug_get_variant.restype = i32
+    L.aug_autotune.argtypes = [i32, vp, i32, u64, vp, vp, vp, vp, i32, vp, vp, vp, sz, vp, i32,
+                               C.POINTER(C.c_int), f32p]
+    L.aug_autotune.restype = i32
+    L.aug_philox4x32_10.argtypes = [vp, i64, u64, vp, vp]
+    L.aug_philox4x32_10.restype = i32
+    L.aug_status_string.argtypes = [i32]
+    L.aug_status_string.restype = C.c_char_p
+    L.aug_version.argtypes = []
+    L.aug_version.restype = i32
+    return L
+
+
+_L = _load()
+
+
+def lib():
+    return _L
+
+
+def status_string(status: int) -> str:
+    return _L.aug_status_string(int(status)).decode()
+
+
+def _check(status: int, where: str):
+    if status != AUG_OK:
+        raise AugError(status, where)
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def _seed(seed: int) -> int:
+    return int(seed) & 0xFFFFFFFFFFFFFFFF
+
+
+# ---- workspace ----------------------------------------------------------------------
+def aug_workspace_size(n_vols: int, n_classes: int = 0) -> int:
+    return int(_L.aug_workspace_size(int(n_vols), int(n_classes)))
+
+
+def make_workspace(n_vols: int, n_classes: int = 0, device=None) -> torch.Tensor:
+    n = aug_workspace_size(n_vols, n_classes)
+    if n == 0:
+        raise AugError(AUG_ERR_INVALID_ARG, "aug_workspace_size")
+    ws = torch.zeros(n + 256, dtype=torch.uint8, device=device or "cuda")
+    off = (-ws.data_ptr()) % 256
+    return ws[off: off + n]
+
+
+def aug_read_device_status(workspace: torch.Tensor, clear: bool = True, stream=None):
+    bad = C.c_int(-1)
+    st = _L.aug_read_device_status(_ptr(workspace), _stream(stream), int(clear), C.byref(bad))
+    return int(st), int(bad.value)
+
+
+# ---- raw entry points (device descriptor arrays) ----------------------------------------
+def aug_warp_fwd(d_descs: torch.Tensor, n_vols: int, seed: int, workspace: torch.Tensor,
+                 stream=None):
+    _check(_L.aug_warp_fwd(_ptr(d_descs), int(n_vols), _seed(seed), _ptr(workspace),
+                           workspace.numel(), _stream(stream)), "aug_warp_fwd")
+
+
+def aug_warp_fwd_volume(h_desc: np.ndarray, seed: int, stream=None):
+    h = np.ascontiguousarray(h_desc, dtype=DESC_DTYPE).reshape(1)
+    _check(_L.aug_warp_fwd_volume(h.ctypes.data_as(C.c_void_p), _seed(seed), _stream(stream)),
+           "aug_warp_fwd_volume")
+
+
+def aug_warp_bwd(d_descs: torch.Tensor, n_vols: int, d_grad_out_ptrs: torch.Tensor,
+                 d_grad_in_ptrs: Optional[torch.Tensor], grad_affine: Optional[torch.Tensor],
+                 workspace: torch.Tensor, stream=None):
+    _check(_L.aug_warp_bwd(_ptr(d_descs), int(n_vols), _ptr(d_grad_out_ptrs),
+                           _ptr(d_grad_in_ptrs), _ptr(grad_affine), _ptr(workspace),
+                           workspace.numel(), _stream(stream)), "aug_warp_bwd")
+
+
+def iou_loss_fwd_bwd(d_descs: torch.Tensor, n_vols: int, p: torch.Tensor, n_classes: int,
+                     loss: torch.Tensor, grad_p: Optional[torch.Tensor],
+                     workspace: torch.Tensor, stream=None):
+    _check(_L.iou_loss_fwd_bwd(_ptr(d_descs), int(n_vols), _ptr(p), int(n_classes),
+                               _ptr(loss), _ptr(grad_p), _ptr(workspace), workspace.numel(),
+                               _stream(stream)), "iou_loss_fwd_bwd")
+
+
+def aug_philox4x32_10(ctr: torch.Tensor, seed: int, stream=None) -> torch.Tensor:
+    """Device Philox4x32-10 words for counters ``ctr`` ([n, 4] int32/uint32 on cuda)."""
+    ctr = ctr.contiguous()
+    out = torch.empty_like(ctr)
+    _check(_L.aug_philox4x32_10(_ptr(ctr), ctr.numel() // 4, _seed(seed), _ptr(out),
+                                _stream(stream)), "aug_philox4x32_10")
+    return out
+
+
+def aug_num_variants(op: int) -> int:
+    return int(_L.aug_num_variants(op))
+
+
+def aug_variant_name(op: int, v: int) -> str:
+    return _L.aug_variant_name(op, v).decode()
+
+
+def aug_set_variant(op: int, v: int):
+    _check(_L.aug_set_variant(op, v), "aug_set_variant")
+
+
+def aug_get_variant(op: int) -> int:
+    return int(_L.aug_get_variant(op))
+
+
+def aug_autotune(op: int, batch: "VolumeBatch", workspace: torch.Tensor, *, seed: int = 0,
+                 grad_out_ptrs=None, grad_in_ptrs=None, grad_affine=None, p=None,
+                 n_classes: int = 0, loss=None, grad_p=None, reps: int = 5, stream=None):
+    best, ms = C.c_int(-1), C.c_float(0.0)
+    _check(_L.aug_autotune(op, _ptr(batch.d_descs), batch.n, _seed(seed), _ptr(grad_out_ptrs),
+                           _ptr(grad_in_ptrs), _ptr(grad_affine), _ptr(p), int(n_classes),
+                           _ptr(loss), _ptr(grad_p), _ptr(workspace), workspace.numel(),
+                           _stream(stream), int(reps), C.byref(best), C.byref(ms)),
+           "aug_autotune")
+    return int(best.value), float(ms.value)
+
+
+def aug_version() -> int:
+    return int(_L.aug_version())
+
+
+# ---- descriptor packing ------------------------------------------------------------------
+def _dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.float32:
+        return AUG_F32
+    if t.dtype == torch.int16:
+        return AUG_I16
+    raise TypeError(f"image dtype must be float32 or int16, got {t.dtype}")
+
+
+class VolumeBatch:
+    """A batch of volume descriptors (host copy + device copy).
+
+    ``images``/``labels``: per volume ``[nz, ny, nx]`` contiguous CUDA tensors
+    (labels uint8 or None).  ``out_images``/``out_labels``: per volume output
+    tensors ``[onz, ony, onx]`` (float32 / uint8) or None.  ``affines``:
+    ``[B, 3, 4]`` float32 (output index -> input coordinate).  The batch keeps
+    references to every tensor it points to.
+    """
+
+    def __init__(self, images: Sequence[Optional[torch.Tensor]], affines, out_shapes,
+                 labels=None, out_images=None, out_labels=None, photo_a=None, photo_b=None,
+                 noise_sigma=None, fill_image=-1000.0, fill_label=0, noise_ids=None,
+                 device=None):
+        B = len(out_shapes)
+        self.n = B
+        h = np.zeros(B, DESC_DTYPE)
+        aff = np.asarray(affines.detach().cpu() if torch.is_tensor(affines) else affines,
+                         np.float32).reshape(B, 12)
+        labels = labels if labels is not None else [None] * B
+        out_images = out_images if out_images is not None else [None] * B
+        out_labels = out_labels if out_labels is not None else [None] * B
+        pa = np.ones(B, np.float32) if photo_a is None else np.asarray(photo_a, np.float32)
+        pb = np.zeros(B, np.float32) if photo_b is None else np.asarray(photo_b, np.float32)
+        ns = np.zeros(B, np.float32) if noise_sigma is None else np.asarray(noise_sigma,
+                                                                              np.float32)
+        fi = np.broadcast_to(np.asarray(fill_image, np.float32), (B,))
+        fl = np.broadcast_to(np.asarray(fill_label, np.int32), (B,))
+        nid = np.arange(B, dtype=np.uint32) if noise_ids is None else np.asarray(noise_ids,
+                                                                                  np.uint32)
+        self._keep = []
+        for b in range(B):
+            img, lab, oi, ol = images[b], labels[b], out_images[b], out_labels[b]
+            if img is not None:
+                assert img.is_cuda and img.is_contiguous() and img.dim() == 3
+                h["image"][b] = img.data_ptr()
+                h["image_dtype"][b] = _dtype_code(img)
+                h["in_nz"][b], h["in_ny"][b], h["in_nx"][b] = img.shape
+            if lab is not None:
+                assert lab.is_cuda and lab.is_contiguous() and lab.dtype == torch.uint8
+                if img is not None:
+                    assert tuple(lab.shape) == tuple(img.shape)
+                else:
+                    h["in_nz"][b], h["in_ny"][b], h["in_nx"][b] = lab.shape
+                h["label"][b] = lab.data_ptr()
+            onx, ony, onz = (int(v) for v in out_shapes[b])
+            h["out_nx"][b], h["out_ny"][b], h["out_nz"][b] = onx, ony, onz
+            if oi is not None:
+                assert oi.is_cuda and oi.is_contiguous() and oi.dtype == torch.float32
+                assert tuple(oi.shape) == (onz, ony, onx)
+                h["out_image"][b] = oi.data_ptr()
+            if ol is not None:
+                assert ol.is_cuda and ol.is_contiguous() and ol.dtype == torch.uint8
+                assert tuple(ol.shape) == (onz, ony, onx)
+                h["out_label"][b] = ol.data_ptr()
+            self._keep += [img, lab, oi, ol]
+        h["affine"] = aff
+        h["photo_a"], h["photo_b"], h["noise_sigma"] = pa, pb, ns
+        h["fill_image"], h["fill_label"], h["noise_id"] = fi, fl, nid
+        self.h_descs = h
+        dev = device or (images[0].device if images[0] is not None else torch.device("cuda"))
+        self.d_descs = torch.from_numpy(h.view(np.uint8).copy()).to(dev)
+
+    def upload(self):
+        """Re-copy the host descriptors to the device (e.g. after editing
+        ``h_descs`` between CUDA-graph replays)."""
+        self.d_descs.copy_(torch.from_numpy(self.h_descs.view(np.uint8).copy()))
+
+    def out_voxels(self):
+        return [int(self.h_descs["out_nx"][b]) * int(self.h_descs["out_ny"][b]) *
+                int(self.h_descs["out_nz"][b]) for b in range(self.n)]
+
+
+def pointer_array(tensors: Sequence[Optional[torch.Tensor]], device) -> torch.Tensor:
+    """Device array of raw pointers (int64) for the adjoint's per-volume buffers."""
+    return torch.tensor([0 if t is None else t.data_ptr() for t in tensors], dtype=torch.int64,
+                        device=device)
+
+
+# ---- autograd wrappers ----------------------------------------------------------------------
+class AugWarp(torch.autograd.Function):
+    """Differentiable warp of a batch of equal-shape float32 volumes.
+
+    forward(image [B, D, H, W], affine [B, 3, 4], out_shape (onx, ony, onz),
+    photo [B, 2] (a, b) or None, sigma [B] or None, seed, fill) ->
+    out [B, onz, ony, onx].  backward returns the gradients with respect to
+    ``image`` and ``affine`` (aug_warp_bwd)."""
+
+    @staticmethod
+    def forward(ctx, image, affine, out_shape, photo=None, sigma=None, seed=0, fill=-1000.0):
+        B = image.shape[0]
+        onx, ony, onz = (int(v) for v in out_shape)
+        image = image.contiguous()
+        out = torch.empty((B, onz, ony, onx), dtype=torch.float32, device=image.device)
+        pa = None if photo is None else photo[:, 0].detach().cpu().numpy()
+        pb = None if photo is None else photo[:, 1].detach().cpu().numpy()
+        sg = None if sigma is None else sigma.detach().cpu().numpy()
+        batch = VolumeBatch([image[b] for b in range(B)], affine, [(onx, ony, onz)] * B,
+                            out_images=[out[b] for b in range(B)], photo_a=pa, photo_b=pb,
+                            noise_sigma=sg, fill_image=fill)
+        ws = make_workspace(B, 0, image.device)
+        aug_warp_fwd(batch.d_descs, B, seed, ws)
+        ctx.save_for_backward(image, affine)
+        ctx.batch, ctx.ws = batch, ws
+        ctx.needs = (ctx.needs_input_grad[0], ctx.needs_input_grad[1])
+        return out
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        image, affine = ctx.saved_tensors
+        B = image.shape[0]
+        g = grad_out.contiguous()
+        gptr = pointer_array([g[b] for b in range(B)], image.device)
+        gin = torch.empty_like(image) if ctx.needs[0] else None
+        giptr = pointer_array([gin[b] for b in range(B)], image.device) if ctx.needs[0] else None
+        gaff = torch.empty((B, 3, 4), dtype=torch.float32, device=image.device) \
+            if ctx.needs[1] else None
+        aug_warp_bwd(ctx.batch.d_descs, B, gptr, giptr, gaff, ctx.ws)
+        return gin, gaff, None, None, None, None, None
+
+
+class IouLoss(torch.autograd.Function):
+    """Soft IOU loss of class probabilities against nearest-warped labels,
+    mean over classes and batch (Sec. 5.C).  forward(p [B, C, onz, ony, onx],
+    labels [B, D, H, W] uint8, affine [B, 3, 4]) -> scalar; the gradient with
+    respect to p comes from the same fused call."""
+
+    @staticmethod
+    def forward(ctx, p, labels, affine):
+        B, Cn = p.shape[0], p.shape[1]
+        onz, ony, onx = p.shape[2:]
+        p = p.contiguous()
+        batch = VolumeBatch([None] * B, affine, [(onx, ony, onz)] * B,
+                            labels=[labels[b] for b in range(B)], device=p.device)
+        ws = make_workspace(B, Cn, p.device)
+        loss = torch.empty(B, dtype=torch.float32, device=p.device)
+        gp = torch.empty_like(p) if ctx.needs_input_grad[0] else None
+        iou_loss_fwd_bwd(batch.d_descs, B, p, Cn, loss, gp, ws)
+        ctx.gp = gp
+        return loss.mean()
+
+    @staticmethod
+    def backward(ctx, grad):
+        return ctx.gp * grad, None, None
