@@ -257,100 +257,108 @@ def run_ours(args, rank, world, local):
     peak, peak_kind = hbm_peak()
     res = {}
 
-    # ---- headline: batched forward, 64 uneven volumes ----------------------------------
-    w1 = workloads.config1(device=dev)
-    for v in w1.vols:
-        v.noise_id += 64 * rank
-    batch, (img_all, lab_all), (oi_all, ol_all) = build_fwd(w1, A)
-    ws = A.make_workspace(batch.n, 6, dev)
-    n_out = sum(batch.out_voxels())
-    alg = fwd_alg_bytes(w1)
-    with torch.cuda.stream(stream):
-        best, best_ms = A.aug_autotune(A.OP_FWD, batch, ws, seed=seed, reps=3)
-    variant = A.aug_variant_name(A.OP_FWD, best)
-    graph = capture(lambda: A.aug_warp_fwd(batch.d_descs, batch.n, seed, ws), stream)
-    # Pre-roll at load so the clock samples see the steady state.
-    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")
-    sampler = ClockSampler(vis[local].strip() if len(vis) > local and vis[local].strip()
-                           else local)
-    t_end = time.time() + 1.0
-    with torch.cuda.stream(stream):
-        while time.time() < t_end:
-            for _ in range(50):
-                graph.replay()
+    if args.only in ("all", "fwd"):
+        # ---- headline: batched forward, 64 uneven volumes ----------------------------------
+        w1 = workloads.config1(device=dev)
+        for v in w1.vols:
+            v.noise_id += 64 * rank
+        batch, (img_all, lab_all), (oi_all, ol_all) = build_fwd(w1, A)
+        ws = A.make_workspace(batch.n, 6, dev)
+        n_out = sum(batch.out_voxels())
+        alg = fwd_alg_bytes(w1)
+        if args.variant >= 0:
+            A.aug_set_variant(A.OP_FWD, args.variant)
+            best = args.variant
+        else:
+            with torch.cuda.stream(stream):
+                best, _ = A.aug_autotune(A.OP_FWD, batch, ws, seed=seed, reps=3)
+        variant = A.aug_variant_name(A.OP_FWD, best)
+        graph = capture(lambda: A.aug_warp_fwd(batch.d_descs, batch.n, seed, ws), stream)
+        # Pre-roll at load so the clock samples see the steady state.
+        vis = os.environ.get("CUDA_VISIBLE_DEVICES", "").split(",")
+        sampler = ClockSampler(vis[local].strip() if len(vis) > local and vis[local].strip()
+                               else local)
+        t_end = time.time() + (0.0 if args.no_preroll else 1.0)
+        with torch.cuda.stream(stream):
+            while time.time() < t_end:
+                for _ in range(50):
+                    graph.replay()
+                torch.cuda.synchronize()
+        ms = time_graph(graph, args.steps, args.warmup, stream)
+        clocks = sampler.stop()
+        st, bad = A.aug_read_device_status(ws)
+        if st != 0:
+            raise RuntimeError(f"device status {A.status_string(st)} volume {bad}")
+        ms_max = D.reduce_max(ms, dev if world > 1 else "cpu")
+        value = world * n_out / (ms_max * 1e-3) / 1e9
+        achieved = alg / (ms * 1e-3) / 1e9
+        res.update(value=value, ms=ms_max, n_out=n_out, alg=alg, achieved=achieved, variant=variant,
+                   clocks=clocks)
+        log(f"[fwd] {variant}: {ms:.4f} ms/step, {n_out / ms / 1e6:.1f} Gvox/s, "
+            f"{achieved:.0f} GB/s algorithmic ({alg / 1e9:.3f} GB/step)")
+
+    if args.only == "all":
+        # ---- plain one-volume-per-launch forward on the same batch ---------------------------
+        def plain():
+            for b in range(batch.n):
+                A.aug_warp_fwd_volume(batch.h_descs[b:b + 1], seed)
+        with torch.cuda.stream(stream):
+            for _ in range(3):
+                plain()
             torch.cuda.synchronize()
-    ms = time_graph(graph, args.steps, args.warmup, stream)
-    clocks = sampler.stop()
-    st, bad = A.aug_read_device_status(ws)
-    if st != 0:
-        raise RuntimeError(f"device status {A.status_string(st)} volume {bad}")
-    ms_max = D.reduce_max(ms, dev if world > 1 else "cpu")
-    value = world * n_out / (ms_max * 1e-3) / 1e9
-    achieved = alg / (ms * 1e-3) / 1e9
-    res.update(value=value, ms=ms_max, n_out=n_out, alg=alg, achieved=achieved, variant=variant,
-               clocks=clocks)
-    log(f"[fwd] {variant}: {ms:.4f} ms/step, {n_out / ms / 1e6:.1f} Gvox/s, "
-        f"{achieved:.0f} GB/s algorithmic ({alg / 1e9:.3f} GB/step)")
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            reps = max(3, min(args.steps, 50))
+            e0.record(stream)
+            for _ in range(reps):
+                plain()
+            e1.record(stream)
+            e1.synchronize()
+        ms_plain = e0.elapsed_time(e1) / reps
+        res["plain"] = {"value": round(n_out / (ms_plain * 1e-3) / 1e9, 3), "unit": "Gvox/s",
+                        "ms_per_step": round(ms_plain, 4), "launches_per_step": batch.n}
+        log(f"[plain] {ms_plain:.4f} ms/step")
 
-    # ---- plain one-volume-per-launch forward on the same batch ---------------------------
-    def plain():
-        for b in range(batch.n):
-            A.aug_warp_fwd_volume(batch.h_descs[b:b + 1], seed)
-    with torch.cuda.stream(stream):
-        for _ in range(3):
-            plain()
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        reps = max(3, min(args.steps, 50))
-        e0.record(stream)
-        for _ in range(reps):
-            plain()
-        e1.record(stream)
-        e1.synchronize()
-    ms_plain = e0.elapsed_time(e1) / reps
-    res["plain"] = {"value": round(n_out / (ms_plain * 1e-3) / 1e9, 3), "unit": "Gvox/s",
-                    "ms_per_step": round(ms_plain, 4), "launches_per_step": batch.n}
-    log(f"[plain] {ms_plain:.4f} ms/step")
+        # ---- end to end through the C ABI from pinned host buffers ------------------------------
+        h_img = torch.empty(img_all.shape, dtype=img_all.dtype, pin_memory=True)
+        h_lab = torch.empty(lab_all.shape, dtype=torch.uint8, pin_memory=True)
+        h_img.copy_(img_all)
+        h_lab.copy_(lab_all)
+        h_oi = torch.empty(oi_all.shape, dtype=torch.float32, pin_memory=True)
+        h_ol = torch.empty(ol_all.shape, dtype=torch.uint8, pin_memory=True)
 
-    # ---- end to end through the C ABI from pinned host buffers ------------------------------
-    h_img = torch.empty(img_all.shape, dtype=img_all.dtype, pin_memory=True)
-    h_lab = torch.empty(lab_all.shape, dtype=torch.uint8, pin_memory=True)
-    h_img.copy_(img_all)
-    h_lab.copy_(lab_all)
-    h_oi = torch.empty(oi_all.shape, dtype=torch.float32, pin_memory=True)
-    h_ol = torch.empty(ol_all.shape, dtype=torch.uint8, pin_memory=True)
-
-    def e2e_step():
-        img_all.copy_(h_img, non_blocking=True)
-        lab_all.copy_(h_lab, non_blocking=True)
-        A.aug_warp_fwd(batch.d_descs, batch.n, seed, ws)
-        h_oi.copy_(oi_all, non_blocking=True)
-        h_ol.copy_(ol_all, non_blocking=True)
-    k_e2e = max(3, min(args.steps, 20))
-    with torch.cuda.stream(stream):
-        for _ in range(2):
-            e2e_step()
-        torch.cuda.synchronize()
-        D.barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(k_e2e):
-            e2e_step()
-        e1.record(stream)
-        e1.synchronize()
-    ms_e2e = D.reduce_max(e0.elapsed_time(e1) / k_e2e, dev if world > 1 else "cpu")
-    res["e2e"] = {"value": round(world * n_out / (ms_e2e * 1e-3) / 1e9, 3), "unit": "Gvox/s",
-                  "h2d_bytes_per_step": int(img_all.numel() * img_all.element_size() +
-                                            lab_all.numel()),
-                  "d2h_bytes_per_step": int(oi_all.numel() * 4 + ol_all.numel()),
-                  "ms_per_step": round(ms_e2e, 3), "steps": k_e2e}
-    log(f"[e2e] {ms_e2e:.3f} ms/step")
-    del h_img, h_lab, h_oi, h_ol
+        def e2e_step():
+            img_all.copy_(h_img, non_blocking=True)
+            lab_all.copy_(h_lab, non_blocking=True)
+            A.aug_warp_fwd(batch.d_descs, batch.n, seed, ws)
+            h_oi.copy_(oi_all, non_blocking=True)
+            h_ol.copy_(ol_all, non_blocking=True)
+        k_e2e = max(3, min(args.steps, 20))
+        with torch.cuda.stream(stream):
+            for _ in range(2):
+                e2e_step()
+            torch.cuda.synchronize()
+            D.barrier()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(k_e2e):
+                e2e_step()
+            e1.record(stream)
+            e1.synchronize()
+        ms_e2e = D.reduce_max(e0.elapsed_time(e1) / k_e2e, dev if world > 1 else "cpu")
+        res["e2e"] = {"value": round(world * n_out / (ms_e2e * 1e-3) / 1e9, 3), "unit": "Gvox/s",
+                      "h2d_bytes_per_step": int(img_all.numel() * img_all.element_size() +
+                                                lab_all.numel()),
+                      "d2h_bytes_per_step": int(oi_all.numel() * 4 + ol_all.numel()),
+                      "ms_per_step": round(ms_e2e, 3), "steps": k_e2e}
+        log(f"[e2e] {ms_e2e:.3f} ms/step")
+        del h_img, h_lab, h_oi, h_ol
 
     # ---- forward + backward, 8 x 128^3 --------------------------------------------------------
-    res["fwd_bwd"] = bench_fwd_bwd(args, A, D, dev, stream, seed, world)
-    if args.all:
+    if args.only in ("all", "fwd_bwd"):
+        res["fwd_bwd"] = bench_fwd_bwd(args, A, D, dev, stream, seed, world)
+    if (args.only == "all" and args.all) or args.only == "iou":
         res["iou"] = bench_iou(args, A, dev, stream)
+    if (args.only == "all" and args.all) or args.only == "train":
         res["train_step"] = bench_train(args, A, dev, stream, seed)
     res["peak"], res["peak_kind"] = peak, peak_kind
     res["launches"] = args.steps  # one kernel per graph replay
@@ -453,10 +461,11 @@ def bench_train(args, A, dev, stream, seed):
 
 
 # ---- CPU baseline: the FP64 oracle ----------------------------------------------------------
-def cpu_baseline(min_seconds=10.0):
+def cpu_baseline(min_seconds=15.0):
     from oracle import ref
     from synth import workloads
-    w = workloads.config1(device="cpu", n_vols=16)
+    # Inputs are generated on the GPU (fast) and copied to the host per volume.
+    w = workloads.config1(device="cuda" if torch.cuda.is_available() else "cpu")
     done, t0 = 0, time.perf_counter()
     nv = 0
     for v in w.vols:
@@ -527,6 +536,11 @@ def main():
     ap.add_argument("--all", action="store_true", help="also time the IOU and training-step "
                     "workloads")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--only", choices=["all", "fwd", "fwd_bwd", "iou", "train"], default="all",
+                    help="time one workload only (profiling runs)")
+    ap.add_argument("--variant", type=int, default=-1,
+                    help="fixed kernel variant instead of autotuning (profiling runs)")
+    ap.add_argument("--no-preroll", action="store_true")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -541,6 +555,11 @@ def main():
     rank, world, local = D.init_from_env("nccl")
     res = run_ours(args, rank, world, local)
     if rank != 0:
+        return
+    if args.only != "all":
+        keep = {k: v for k, v in res.items() if k in ("fwd_bwd", "iou", "train_step", "ms",
+                                                       "value", "variant", "achieved")}
+        print(json.dumps({"profile_run": args.only, **keep}), flush=True)
         return
     cpu = None
     if world == 1 and not args.no_cpu_baseline:

@@ -87,9 +87,12 @@ def test_config2_full_size():
 
 
 def test_int16_affine_gradient():
-    w = workloads.config4(device="cuda", n_vols=1)
-    v = w.vols[0]
-    v.out_shape = (64, 48, 40)  # a smaller crop of the same full-resolution volume
+    # Full-resolution int16 input, 3 mm / 0.7 mm downscale, a smaller crop
+    # centred like the full-size one.
+    down = 3.0 / 0.7
+    spec = AffineSpec(max_shift_vox=10.0 * down, extra_scale=(down, down, down))
+    v = make_case((512, 512, 333), (64, 48, 40), seed=401, dtype="int16", device="cuda",
+                  spec=spec)
     g = upstream_grads([v.out_shape], seed=13, device="cuda")
     _, gaff = run_bwd([v], g, want_gin=False)
     _, rt, _ = ref.warp_bwd(v, g[0], want_grad_in=False)
