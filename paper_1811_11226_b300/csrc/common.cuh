@@ -5,7 +5,7 @@
 // |T| >= 2^-17 is exact in Q.40 and integer output indices are exact, so the
 // coordinate equals the real-number value A o + b exactly; floor/round
 // decisions (cell choice, nearest label) are therefore exact, and only the
-// interpolation weight is rounded (to 24 bits).  Float32 coordinates would be
+// interpolation weight is rounded (to 23 bits).  Float32 coordinates would be
 // off by up to ~1.5e-5 voxel at |s| ~ 200, i.e. ~0.02 HU at a 1000 HU edge.
 #pragma once
 
@@ -109,11 +109,14 @@ __device__ __forceinline__ int q40_hi(long long s) { return (int)(s >> 32); }
 __device__ __forceinline__ int q40_floor(long long s) { return q40_hi(s) >> 8; }
 // floor(s + 1/2): adding 2^39 only touches the high word.
 __device__ __forceinline__ int q40_round(long long s) { return (q40_hi(s) + 128) >> 8; }
-// s - floor(s), truncated to 24 bits (error < 2^-24).
+// s - floor(s), truncated to 23 bits (error < 2^-23): the top 23 fractional
+// bits become the mantissa of a float in [1, 2), minus 1 (exact).
 __device__ __forceinline__ float q40_frac(long long s) {
-  const unsigned m = (unsigned)((unsigned long long)s >> 16) & 0xFFFFFFu;
-  return __uint2float_rn(m) * 5.9604644775390625e-8f;
+  const unsigned m = (unsigned)((unsigned long long)s >> 17) & 0x7FFFFFu;
+  return __uint_as_float(0x3F800000u | m) - 1.0f;
 }
+// Bit 39 of s: 1 when frac(s) >= 1/2, i.e. floor(s + 1/2) = floor(s) + bit.
+__device__ __forceinline__ int q40_halfbit(long long s) { return (q40_hi(s) >> 7) & 1; }
 
 template <typename T>
 __device__ __forceinline__ float ld_val(const T* p);
@@ -136,21 +139,59 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, unsigned k0, unsigned k1
       k0 += 0x9E3779B9u;
       k1 += 0xBB67AE85u;
     }
-    const unsigned lo0 = 0xD2511F53u * c.x, hi0 = __umulhi(0xD2511F53u, c.x);
-    const unsigned lo1 = 0xCD9E8D57u * c.z, hi1 = __umulhi(0xCD9E8D57u, c.z);
-    c = make_uint4(hi1 ^ c.y ^ k0, lo1, hi0 ^ c.w ^ k1, lo0);
+    const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+    const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+    c = make_uint4((unsigned)(p1 >> 32) ^ c.y ^ k0, (unsigned)p1, (unsigned)(p0 >> 32) ^ c.w ^ k1,
+                   (unsigned)p0);
   }
   return c;
 }
 
-// Box-Muller on one pair of words: (R cos 2 pi u2, R sin 2 pi u2).
+// Documented approximate PTX instructions (special-function unit).
+__device__ __forceinline__ float lg2_approx(float x) {
+  float r;
+  asm("lg2.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float r;
+  asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float sin_approx(float x) {
+  float r;
+  asm("sin.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float cos_approx(float x) {
+  float r;
+  asm("cos.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// Box-Muller on one pair of words: (R cos 2 pi u2, R sin 2 pi u2) with
+// u1 = ((ra >> 8) + 1) 2^-24 in (0, 1], u2 = (rb >> 8) 2^-24 in [0, 1),
+// R = sqrt(-2 ln u1).
+//
+// -2 ln u1: for v = 1 - u1 < 2^-6 (exact in float) the series
+// 2 v (1 + v/2 + v^2/3 + v^3/4) (Taylor series of -2 ln(1 - v), relative
+// truncation error < v^4/5 < 2e-8) keeps full relative accuracy where R is
+// small; otherwise -2 ln 2 * log2(u1) with the hardware log2 (absolute error
+// ~2^-22), which changes R by < 1e-6 there since R > 0.17.  R uses the
+// hardware square root (relative error ~2^-23).  The angle is
+// a = 2 pi u2 - pi in [-pi, pi), where the hardware sine/cosine have absolute
+// error ~2^-21, and cos(2 pi u2) = -cos a, sin(2 pi u2) = -sin a.  Overall
+// |n - n_exact| < ~5e-6 for |n| <= 5.8, i.e. < 2.5e-4 HU at sigma = 50.
 __device__ __forceinline__ float2 box_muller(unsigned ra, unsigned rb) {
-  const float u1 = (float)((ra >> 8) + 1u) * 5.9604644775390625e-8f;  // (0, 1], exact
-  const float u2 = (float)(rb >> 8) * 5.9604644775390625e-8f;          // [0, 1), exact
-  const float r = sqrtf(-2.0f * logf(u1));
-  float s, c;
-  sincospif(2.0f * u2, &s, &c);
-  return make_float2(r * c, r * s);
+  const unsigned m1 = ra >> 8, m2 = rb >> 8;
+  const float u1 = (float)(m1 + 1u) * 5.9604644775390625e-8f;
+  const float v = (float)(0xFFFFFFu - m1) * 5.9604644775390625e-8f;  // 1 - u1, exact
+  const float series =
+      2.0f * v * fmaf(v, fmaf(v, fmaf(v, 0.25f, 0.333333333f), 0.5f), 1.0f);
+  const float x = (v < 0.015625f) ? series : -1.38629436112f * lg2_approx(u1);
+  const float r = sqrt_approx(x);
+  const float a = fmaf((float)m2 * 5.9604644775390625e-8f, 6.28318530718f, -3.14159265359f);
+  return make_float2(-r * cos_approx(a), -r * sin_approx(a));
 }
 
 // Four normals of one quad (lanes 0..3).

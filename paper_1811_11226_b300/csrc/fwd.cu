@@ -8,82 +8,171 @@
 //    the input they gather from stays in L2.
 //  * k_fwd_volume: the plain form -- one launch per volume, one CTA per tile,
 //    descriptor passed by value.
+//
+// Each thread walks its z-run one quad (4 z-consecutive voxels, one Philox
+// call) at a time.  The warp re-classifies every quad (interior / exterior /
+// general, from the quad's first and last coordinates), so only quads that
+// actually straddle the input boundary pay for per-tap checks.
 #include "kernels.h"
 #include "sample.cuh"
 
 namespace augk {
 
-// One z-run of one thread (4*QZ voxels at most), for a warp-uniform MODE.
-template <typename TIn, int MODE, int QZ>
-__device__ __forceinline__ void fwd_run(const VolConst& vc, const TileCoord& tc, long long sx,
-                                        long long sy, long long sz, unsigned key0,
-                                        unsigned key1) {
-  const TIn* __restrict__ img = (const TIn*)vc.image;
-  const long long dx = vc.tq[0][2], dy = vc.tq[1][2], dz = vc.tq[2][2];
-  const int nx = vc.nx, ny = vc.ny, nz = vc.nz;
-  const int onx = vc.onx, ony = vc.ony;
-  const int plane = onx * ony;
-  float* __restrict__ out_img = vc.out_image;
-  uint8_t* __restrict__ out_lab = vc.out_label;
-  const bool want_img = out_img != nullptr, want_lab = out_lab != nullptr;
-  const bool noisy = vc.sigma > 0.0f;
-  const float a = vc.a, b = vc.b, sigma = vc.sigma, fill = vc.fill;
-  int o = (tc.k0 * ony + tc.jc) * onx + tc.ic;
-#pragma unroll 1
-  for (int q = 0; q < QZ; ++q) {
-    const int kq = tc.k0 + 4 * q;
-    if (kq >= tc.k1) break;
-    float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    if (noisy && want_img)
-      quad_normals(((unsigned long long)(kq >> 2) * (unsigned)ony + (unsigned)tc.jc) *
-                           (unsigned)onx + (unsigned)tc.ic,
-                   vc.noise_id, key0, key1, z);
-#pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      if (kq + m < tc.k1) {
-        if (want_img) {
-          Taps t;
-          load_taps<TIn, MODE>(img, sx, sy, sz, nx, ny, nz, fill, t);
-          float c00, c10, c01, c11, c0, c1;
-          const float v = trilerp(t, c00, c10, c01, c11, c0, c1);
-          const float y = fmaf(sigma, z[m], fmaf(a, v, b));
-          if (tc.valid) __stcs(out_img + o, y);
-        }
-        if (want_lab) {
-          const int l = load_label<MODE>(vc.label, sx, sy, sz, nx, ny, nz, vc.fill_label);
-          if (tc.valid) out_lab[o] = (uint8_t)l;
-        }
-        sx += dx;
-        sy += dy;
-        sz += dz;
-        o += plane;
+// Per-tile copy of the volume constants, held in registers.
+template <typename TIn>
+struct FwdP {
+  const TIn* img;
+  const uint8_t* lab;
+  float* oimg;
+  uint8_t* olab;
+  long long dx, dy, dz;
+  int nx, ny, nz, nxy, plane, fill_label;
+  float a, b, sigma, fill;
+};
+
+// One output voxel at coordinate (sx, sy, sz).
+template <typename TIn, int MODE, bool IMG, bool LAB>
+__device__ __forceinline__ void fwd_voxel(const FwdP<TIn>& P, long long sx, long long sy,
+                                          long long sz, float z, int o, bool valid) {
+  float v = P.fill;
+  int lab = P.fill_label;
+  if (MODE != MODE_EXTERIOR) {
+    const int fx = q40_floor(sx), fy = q40_floor(sy), fz = q40_floor(sz);
+    const int hbx = q40_halfbit(sx), hby = q40_halfbit(sy), hbz = q40_halfbit(sz);
+    if (MODE == MODE_INTERIOR) {
+      const int base = (fz * P.ny + fy) * P.nx + fx;
+      if (IMG) {
+        const TIn* p = P.img + base;
+        Taps t;
+        t.v000 = ld_val(p);
+        t.v100 = ld_val(p + 1);
+        t.v010 = ld_val(p + P.nx);
+        t.v110 = ld_val(p + P.nx + 1);
+        t.v001 = ld_val(p + P.nxy);
+        t.v101 = ld_val(p + P.nxy + 1);
+        t.v011 = ld_val(p + P.nxy + P.nx);
+        t.v111 = ld_val(p + P.nxy + P.nx + 1);
+        t.tx = q40_frac(sx);
+        t.ty = q40_frac(sy);
+        t.tz = q40_frac(sz);
+        float c00, c10, c01, c11, c0, c1;
+        v = trilerp(t, c00, c10, c01, c11, c0, c1);
       }
+      if (LAB) lab = __ldg(P.lab + (base + hbx + hby * P.nx + hbz * P.nxy));
+    } else {
+      if (IMG) {
+        Taps t;
+        load_taps<TIn, MODE_GENERAL>(P.img, sx, sy, sz, P.nx, P.ny, P.nz, P.fill, t);
+        float c00, c10, c01, c11, c0, c1;
+        v = trilerp(t, c00, c10, c01, c11, c0, c1);
+      }
+      if (LAB) {
+        const int rx = fx + hbx, ry = fy + hby, rz = fz + hbz;
+        const bool in = (unsigned)rx < (unsigned)P.nx && (unsigned)ry < (unsigned)P.ny &&
+                        (unsigned)rz < (unsigned)P.nz;
+        if (in) lab = __ldg(P.lab + ((rz * P.ny + ry) * P.nx + rx));
+      }
+    }
+  }
+  if (valid) {
+    if (IMG) __stcs(P.oimg + o, fmaf(P.sigma, z, fmaf(P.a, v, P.b)));
+    if (LAB) P.olab[o] = (uint8_t)lab;
+  }
+}
+
+// n (1..4) voxels of one quad for a warp-uniform MODE.
+template <typename TIn, int MODE, bool IMG, bool LAB>
+__device__ __forceinline__ void fwd_quad(const FwdP<TIn>& P, long long& sx, long long& sy,
+                                         long long& sz, const float z[4], int& o, int n,
+                                         bool valid) {
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    if (m < n) {
+      fwd_voxel<TIn, MODE, IMG, LAB>(P, sx, sy, sz, z[m], o, valid);
+      sx += P.dx;
+      sy += P.dy;
+      sz += P.dz;
+      o += P.plane;
     }
   }
 }
 
-template <typename TIn, int NW, int QZ>
-__device__ __forceinline__ void fwd_tile(const VolConst& vc, int t, unsigned key0,
-                                         unsigned key1) {
+template <typename TIn, int NW, int QZ, bool IMG, bool LAB>
+__device__ __forceinline__ void fwd_tile_t(const VolConst& vc, int t, unsigned key0,
+                                           unsigned key1) {
   const TileCoord tc = tile_coord<NW, QZ>(t, vc.onx, vc.ony, vc.onz);
-  long long s[3], ds[3];
-#pragma unroll
-  for (int r = 0; r < 3; ++r) {
-    s[r] = coord_q40(vc.tq[r], tc.ic, tc.jc, tc.k0);
-    ds[r] = vc.tq[r][2];
+  FwdP<TIn> P;
+  P.img = (const TIn*)vc.image;
+  P.lab = vc.label;
+  P.oimg = vc.out_image;
+  P.olab = vc.out_label;
+  P.dx = vc.tq[0][2];
+  P.dy = vc.tq[1][2];
+  P.dz = vc.tq[2][2];
+  P.nx = vc.nx;
+  P.ny = vc.ny;
+  P.nz = vc.nz;
+  P.nxy = vc.nx * vc.ny;
+  P.plane = vc.onx * vc.ony;
+  P.fill_label = vc.fill_label;
+  P.a = vc.a;
+  P.b = vc.b;
+  P.sigma = vc.sigma;
+  P.fill = vc.fill;
+  const unsigned noise_id = vc.noise_id;
+  const bool noisy = IMG && vc.sigma > 0.0f;
+  const unsigned onx = (unsigned)vc.onx, ony = (unsigned)vc.ony;
+  long long sx = coord_q40(vc.tq[0], tc.ic, tc.jc, tc.k0);
+  long long sy = coord_q40(vc.tq[1], tc.ic, tc.jc, tc.k0);
+  long long sz = coord_q40(vc.tq[2], tc.ic, tc.jc, tc.k0);
+  const long long ds[3] = {P.dx, P.dy, P.dz};
+  int o = (tc.k0 * vc.ony + tc.jc) * vc.onx + tc.ic;
+#pragma unroll 1
+  for (int q = 0; q < QZ; ++q) {
+    const int kq = tc.k0 + 4 * q;
+    if (kq >= tc.k1) break;
+    const int n = min(4, tc.k1 - kq);
+    float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    if (noisy)
+      quad_normals(((unsigned long long)(kq >> 2) * ony + (unsigned)tc.jc) * onx +
+                       (unsigned)tc.ic,
+                   noise_id, key0, key1, z);
+    const long long s[3] = {sx, sy, sz};
+    const int mode = warp_mode(classify_run<true>(s, ds, n - 1, P.nx, P.ny, P.nz));
+    if (mode == MODE_INTERIOR)
+      fwd_quad<TIn, MODE_INTERIOR, IMG, LAB>(P, sx, sy, sz, z, o, n, tc.valid);
+    else if (mode == MODE_EXTERIOR)
+      fwd_quad<TIn, MODE_EXTERIOR, IMG, LAB>(P, sx, sy, sz, z, o, n, tc.valid);
+    else
+      fwd_quad<TIn, MODE_GENERAL, IMG, LAB>(P, sx, sy, sz, z, o, n, tc.valid);
   }
-  const int mode =
-      warp_mode(classify_run<true>(s, ds, tc.k1 - 1 - tc.k0, vc.nx, vc.ny, vc.nz));
-  if (mode == MODE_INTERIOR)
-    fwd_run<TIn, MODE_INTERIOR, QZ>(vc, tc, s[0], s[1], s[2], key0, key1);
-  else if (mode == MODE_EXTERIOR)
-    fwd_run<TIn, MODE_EXTERIOR, QZ>(vc, tc, s[0], s[1], s[2], key0, key1);
-  else
-    fwd_run<TIn, MODE_GENERAL, QZ>(vc, tc, s[0], s[1], s[2], key0, key1);
 }
 
 template <int NW, int QZ>
-__global__ void __launch_bounds__(NW * 32)
+__device__ __forceinline__ void fwd_tile(const VolConst& vc, int t, unsigned key0,
+                                         unsigned key1) {
+  const bool img = vc.out_image != nullptr, lab = vc.out_label != nullptr;
+  if (vc.dtype == AUG_I16) {
+    if (img && lab)
+      fwd_tile_t<int16_t, NW, QZ, true, true>(vc, t, key0, key1);
+    else if (img)
+      fwd_tile_t<int16_t, NW, QZ, true, false>(vc, t, key0, key1);
+    else
+      fwd_tile_t<int16_t, NW, QZ, false, true>(vc, t, key0, key1);
+  } else {
+    if (img && lab)
+      fwd_tile_t<float, NW, QZ, true, true>(vc, t, key0, key1);
+    else if (img)
+      fwd_tile_t<float, NW, QZ, true, false>(vc, t, key0, key1);
+    else
+      fwd_tile_t<float, NW, QZ, false, true>(vc, t, key0, key1);
+  }
+}
+
+// MB: minimum resident CTAs per SM requested from the register allocator
+// (1 = no constraint); part of the variant, chosen by measurement.
+template <int NW, int QZ, int MB>
+__global__ void __launch_bounds__(NW * 32, MB)
     k_fwd_batched(const aug_volume_desc* __restrict__ descs, int n_vols, unsigned key0,
                   unsigned key1, WsHeader* ws) {
   __shared__ VolConst vc;
@@ -95,28 +184,21 @@ __global__ void __launch_bounds__(NW * 32)
     if (!vc.ok) continue;
     const int nt = tiles_in<NW, QZ>(vc.onx, vc.ony, vc.onz);
     if (vc.out_image != nullptr || vc.out_label != nullptr) {
-      for (long long t = first_tile(base); t < nt; t += gridDim.x) {
-        if (vc.dtype == AUG_I16)
-          fwd_tile<int16_t, NW, QZ>(vc, (int)t, key0, key1);
-        else
-          fwd_tile<float, NW, QZ>(vc, (int)t, key0, key1);
-      }
+      for (long long t = first_tile(base); t < nt; t += gridDim.x)
+        fwd_tile<NW, QZ>(vc, (int)t, key0, key1);
     }
     base += nt;
   }
 }
 
-template <int NW, int QZ>
-__global__ void __launch_bounds__(NW * 32)
+template <int NW, int QZ, int MB>
+__global__ void __launch_bounds__(NW * 32, MB)
     k_fwd_volume(const aug_volume_desc desc, unsigned key0, unsigned key1) {
   __shared__ VolConst vc;
   stage_volume(&desc, 0, vc, nullptr, desc.out_image != nullptr, false);
   __syncthreads();
   if (!vc.ok) return;
-  if (vc.dtype == AUG_I16)
-    fwd_tile<int16_t, NW, QZ>(vc, blockIdx.x, key0, key1);
-  else
-    fwd_tile<float, NW, QZ>(vc, blockIdx.x, key0, key1);
+  fwd_tile<NW, QZ>(vc, blockIdx.x, key0, key1);
 }
 
 // ---- host launchers ----------------------------------------------------------
@@ -126,13 +208,15 @@ struct FwdVariant {
   const void* batched;
   const void* volume;
 };
-#define FWD_V(NW, QZ) \
-  { NW, QZ, (const void*)k_fwd_batched<NW, QZ>, (const void*)k_fwd_volume<NW, QZ> }
-const FwdVariant kFwd[] = {FWD_V(8, 4),  FWD_V(4, 4), FWD_V(8, 2), FWD_V(8, 8),
-                           FWD_V(4, 8),  FWD_V(16, 2), FWD_V(2, 8)};
+#define FWD_V(NW, QZ, MB) \
+  { NW, QZ, (const void*)k_fwd_batched<NW, QZ, MB>, (const void*)k_fwd_volume<NW, QZ, MB> }
+const FwdVariant kFwd[] = {FWD_V(4, 8, 1),  FWD_V(4, 8, 12), FWD_V(8, 4, 1), FWD_V(8, 4, 6),
+                           FWD_V(4, 4, 12), FWD_V(8, 8, 6),  FWD_V(8, 2, 6), FWD_V(16, 2, 3),
+                           FWD_V(2, 8, 24)};
 #undef FWD_V
-const char* kFwdNames[] = {"tile32x8x16", "tile32x4x16", "tile32x8x8", "tile32x8x32",
-                           "tile32x4x32", "tile32x16x8", "tile32x2x32"};
+const char* kFwdNames[] = {"tile32x4x32",       "tile32x4x32_48w", "tile32x8x16",
+                           "tile32x8x16_48w",   "tile32x4x16_48w", "tile32x8x32_48w",
+                           "tile32x8x8_48w",    "tile32x16x8_48w", "tile32x2x32_48w"};
 }  // namespace
 
 int fwd_num_variants() { return (int)(sizeof(kFwd) / sizeof(kFwd[0])); }
