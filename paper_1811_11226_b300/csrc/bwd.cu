@@ -17,6 +17,7 @@
 // by k_bwd_finalize: bitwise reproducible.
 #include "kernels.h"
 #include "sample.cuh"
+#include "sched.cuh"
 
 namespace augk {
 
@@ -148,30 +149,45 @@ __global__ void __launch_bounds__(NW * 32)
     k_bwd_batched(const aug_volume_desc* __restrict__ descs, int n_vols,
                   const float* const* gout, float* const* gin, double* partials, WsHeader* ws) {
   __shared__ BwdShared<NW> sh;
-  long long base = 0;
-  for (int v = 0; v < n_vols; ++v) {
-    __syncthreads();
-    stage_volume(descs + v, v, sh.vc, ws, true, GIN);
-    if (threadIdx.x < 12) sh.acc[threadIdx.x] = 0.0;
-    __syncthreads();
-    const float* g = gout[v];
-    float* gi = GIN ? gin[v] : nullptr;
-    const bool ok = sh.vc.ok && g != nullptr && (!GIN || gi != nullptr);
-    if (!ok && sh.vc.ok && blockIdx.x == 0 && threadIdx.x == 0)
-      record_error(ws, AUG_ERR_DESCRIPTOR, v);
-    const int nt = sh.vc.ok ? tiles_in<NW, QZ>(sh.vc.onx, sh.vc.ony, sh.vc.onz) : 0;
-    if (ok) {
-      for (long long t = first_tile(base); t < nt; t += gridDim.x) {
-        if (sh.vc.dtype == AUG_I16)
-          bwd_tile<int16_t, NW, QZ, GIN, GT>(sh, (int)t, g, gi);
-        else
-          bwd_tile<float, NW, QZ, GIN, GT>(sh, (int)t, g, gi);
-      }
-    }
-    if (GT && threadIdx.x < 12)
-      partials[((size_t)blockIdx.x * n_vols + v) * 12 + threadIdx.x] = sh.acc[threadIdx.x];
-    base += nt;
-  }
+  __shared__ aug_volume_desc raw;
+  __shared__ SchedSmem<NW * 32> sm;
+  int staged = -1;
+  const float* g = nullptr;
+  float* gi = nullptr;
+  auto flush = [&]() {
+    // Each of threads 0..11 wrote its own sh.acc entry: no barrier needed.
+    if (GT && staged >= 0 && threadIdx.x < 12)
+      partials[((size_t)blockIdx.x * n_vols + staged) * 12 + threadIdx.x] = sh.acc[threadIdx.x];
+  };
+  for_each_tile<NW, QZ>(
+      descs, n_vols, sm,
+      [&](int c0, int cnt) {
+        validate_chunk(descs, c0, cnt, ws, NEED_IMAGE_ALWAYS, GIN, [&](int v) {
+          return gout[v] != nullptr && (!GIN || gin[v] != nullptr);
+        });
+        // This CTA's partials of the chunk's volumes start at zero (volumes in
+        // which it has no tile keep them).
+        if (GT)
+          for (int i = threadIdx.x; i < cnt * 12; i += blockDim.x)
+            partials[((size_t)blockIdx.x * n_vols + c0) * 12 + i] = 0.0;
+      },
+      [&](int v, int t, long long) {
+        if (v != staged) {
+          flush();
+          stage_volume_fast(descs + v, v, sh.vc, raw, NEED_IMAGE_ALWAYS, GIN);
+          if (threadIdx.x < 12) sh.acc[threadIdx.x] = 0.0;
+          staged = v;
+          g = gout[v];
+          gi = GIN ? gin[v] : nullptr;
+        }
+        if (sh.vc.ok && g != nullptr && (!GIN || gi != nullptr)) {
+          if (sh.vc.dtype == AUG_I16)
+            bwd_tile<int16_t, NW, QZ, GIN, GT>(sh, t, g, gi);
+          else
+            bwd_tile<float, NW, QZ, GIN, GT>(sh, t, g, gi);
+        }
+      });
+  flush();
 }
 
 // Zero every grad_in volume (float32 input shape) before the scatter.

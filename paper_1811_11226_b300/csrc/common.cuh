@@ -46,10 +46,36 @@ struct VolConst {
   int ok;
 };
 
-// Threads of the CTA cooperate; the caller must __syncthreads() afterwards.
-// Validates the descriptor; ok = 0 marks it invalid (the error is recorded by
-// CTA 0 only).  need_image: out_image requires an image of a known dtype;
-// f32_only: the image must be float32.
+// Full check of one descriptor (pure).  need_image: an image of a known
+// dtype is required when out_image is set (forward) or always (adjoint);
+// f32_only: the image must be float32 (adjoint with grad_in).
+__device__ inline bool desc_valid(const aug_volume_desc& d, bool need_image, bool f32_only) {
+  bool ok = true;
+  ok &= d.in_nx >= 1 && d.in_ny >= 1 && d.in_nz >= 1 && d.in_nx <= MAX_DIM &&
+        d.in_ny <= MAX_DIM && d.in_nz <= MAX_DIM;
+  ok &= d.out_nx >= 1 && d.out_ny >= 1 && d.out_nz >= 1 && d.out_nx <= MAX_DIM &&
+        d.out_ny <= MAX_DIM && d.out_nz <= MAX_DIM;
+  ok &= (long long)d.in_nx * d.in_ny * d.in_nz < (1LL << 31);
+  ok &= (long long)d.out_nx * d.out_ny * d.out_nz < (1LL << 31);
+  ok &= d.fill_label >= 0 && d.fill_label <= 255;
+  for (int m = 0; m < 12; ++m) {
+    const float t = d.affine[m];
+    ok &= isfinite(t) && fabsf(t) <= (((m & 3) < 3) ? 64.0f : 1048576.0f);
+  }
+  ok &= isfinite(d.photo_a) && isfinite(d.photo_b) && isfinite(d.noise_sigma) &&
+        d.noise_sigma >= 0.0f && isfinite(d.fill_image);
+  ok &= d.reserved[0] == 0u && d.reserved[1] == 0u && d.reserved[2] == 0u;
+  if (need_image) {
+    ok &= d.image != nullptr && (d.image_dtype == AUG_F32 || d.image_dtype == AUG_I16);
+    if (f32_only) ok &= d.image_dtype == AUG_F32;
+  }
+  ok &= !(d.out_label != nullptr && d.label == nullptr);
+  return ok;
+}
+
+// Parses a descriptor into per-volume constants (threads 0..11 convert the
+// affine to Q.40, thread 0 the rest).  The caller synchronises afterwards.
+// Errors are recorded by the caller's validation pass, not here.
 __device__ inline void stage_volume(const aug_volume_desc* __restrict__ d, int v, VolConst& vc,
                                     WsHeader* ws, bool need_image, bool f32_only) {
   if (threadIdx.x < 12) {
@@ -78,28 +104,10 @@ __device__ inline void stage_volume(const aug_volume_desc* __restrict__ d, int v
     vc.sigma = d->noise_sigma;
     vc.fill = d->fill_image;
     vc.noise_id = d->noise_id;
-    bool ok = true;
-    ok &= vc.nx >= 1 && vc.ny >= 1 && vc.nz >= 1 && vc.nx <= MAX_DIM && vc.ny <= MAX_DIM &&
-          vc.nz <= MAX_DIM;
-    ok &= vc.onx >= 1 && vc.ony >= 1 && vc.onz >= 1 && vc.onx <= MAX_DIM &&
-          vc.ony <= MAX_DIM && vc.onz <= MAX_DIM;
-    ok &= (long long)vc.nx * vc.ny * vc.nz < (1LL << 31);
-    ok &= (long long)vc.onx * vc.ony * vc.onz < (1LL << 31);
-    ok &= vc.fill_label >= 0 && vc.fill_label <= 255;
-    for (int m = 0; m < 12; ++m) {
-      const float t = d->affine[m];
-      ok &= isfinite(t) && fabsf(t) <= (((m & 3) < 3) ? 64.0f : 1048576.0f);
-    }
-    ok &= isfinite(vc.a) && isfinite(vc.b) && isfinite(vc.sigma) && vc.sigma >= 0.0f &&
-          isfinite(vc.fill);
-    ok &= d->reserved[0] == 0u && d->reserved[1] == 0u && d->reserved[2] == 0u;
-    if (need_image) {
-      ok &= vc.image != nullptr && (vc.dtype == AUG_F32 || vc.dtype == AUG_I16);
-      if (f32_only) ok &= vc.dtype == AUG_F32;
-    }
-    ok &= !(vc.out_label != nullptr && vc.label == nullptr);
+    const bool ok = desc_valid(*d, need_image, f32_only);
     vc.ok = ok ? 1 : 0;
-    if (!ok && blockIdx.x == 0) record_error(ws, AUG_ERR_DESCRIPTOR, v);
+    // Kernels without a validation pass (one volume per launch) record here.
+    if (!ok && ws != nullptr && blockIdx.x == 0) record_error(ws, AUG_ERR_DESCRIPTOR, v);
   }
 }
 

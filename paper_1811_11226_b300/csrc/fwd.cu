@@ -15,6 +15,7 @@
 // actually straddle the input boundary pay for per-tap checks.
 #include "kernels.h"
 #include "sample.cuh"
+#include "sched.cuh"
 
 namespace augk {
 
@@ -30,68 +31,94 @@ struct FwdP {
   float a, b, sigma, fill;
 };
 
-// One output voxel at coordinate (sx, sy, sz).
-template <typename TIn, int MODE, bool IMG, bool LAB>
-__device__ __forceinline__ void fwd_voxel(const FwdP<TIn>& P, long long sx, long long sy,
-                                          long long sz, float z, int o, bool valid) {
-  float v = P.fill;
-  int lab = P.fill_label;
-  if (MODE != MODE_EXTERIOR) {
-    const int fx = q40_floor(sx), fy = q40_floor(sy), fz = q40_floor(sz);
-    const int hbx = q40_halfbit(sx), hby = q40_halfbit(sy), hbz = q40_halfbit(sz);
-    if (MODE == MODE_INTERIOR) {
-      const int base = (fz * P.ny + fy) * P.nx + fx;
-      if (IMG) {
-        const TIn* p = P.img + base;
-        Taps t;
-        t.v000 = ld_val(p);
-        t.v100 = ld_val(p + 1);
-        t.v010 = ld_val(p + P.nx);
-        t.v110 = ld_val(p + P.nx + 1);
-        t.v001 = ld_val(p + P.nxy);
-        t.v101 = ld_val(p + P.nxy + 1);
-        t.v011 = ld_val(p + P.nxy + P.nx);
-        t.v111 = ld_val(p + P.nxy + P.nx + 1);
-        t.tx = q40_frac(sx);
-        t.ty = q40_frac(sy);
-        t.tz = q40_frac(sz);
-        float c00, c10, c01, c11, c0, c1;
-        v = trilerp(t, c00, c10, c01, c11, c0, c1);
-      }
-      if (LAB) lab = __ldg(P.lab + (base + hbx + hby * P.nx + hbz * P.nxy));
-    } else {
-      if (IMG) {
-        Taps t;
-        load_taps<TIn, MODE_GENERAL>(P.img, sx, sy, sz, P.nx, P.ny, P.nz, P.fill, t);
-        float c00, c10, c01, c11, c0, c1;
-        v = trilerp(t, c00, c10, c01, c11, c0, c1);
-      }
-      if (LAB) {
-        const int rx = fx + hbx, ry = fy + hby, rz = fz + hbz;
-        const bool in = (unsigned)rx < (unsigned)P.nx && (unsigned)ry < (unsigned)P.ny &&
-                        (unsigned)rz < (unsigned)P.nz;
-        if (in) lab = __ldg(P.lab + ((rz * P.ny + ry) * P.nx + rx));
-      }
-    }
-  }
-  if (valid) {
-    if (IMG) __stcs(P.oimg + o, fmaf(P.sigma, z, fmaf(P.a, v, P.b)));
-    if (LAB) P.olab[o] = (uint8_t)lab;
-  }
-}
-
-// n (1..4) voxels of one quad for a warp-uniform MODE.
+// One quad (n = 1..4 z-consecutive voxels) for a warp-uniform MODE,
+// software-pipelined: every tap and label load of the quad is issued first,
+// the quad's Philox + Box-Muller normals are computed while they are in
+// flight, and only then are the samples interpolated and stored.
 template <typename TIn, int MODE, bool IMG, bool LAB>
 __device__ __forceinline__ void fwd_quad(const FwdP<TIn>& P, long long& sx, long long& sy,
-                                         long long& sz, const float z[4], int& o, int n,
-                                         bool valid) {
+                                         long long& sz, int& o, int n, bool valid, bool noisy,
+                                         unsigned long long quad, unsigned noise_id,
+                                         unsigned key0, unsigned key1) {
+  float tap[4][8];
+  int lab[4];
+  const long long s0x = sx, s0y = sy, s0z = sz;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    lab[m] = P.fill_label;
+#pragma unroll
+    for (int d = 0; d < 8; ++d) tap[m][d] = P.fill;
+    if (MODE != MODE_EXTERIOR && m < n) {
+      const int fx = q40_floor(sx), fy = q40_floor(sy), fz = q40_floor(sz);
+      const int hbx = q40_halfbit(sx), hby = q40_halfbit(sy), hbz = q40_halfbit(sz);
+      if (MODE == MODE_INTERIOR) {
+        const int base = (fz * P.ny + fy) * P.nx + fx;
+        if (IMG) {
+          const TIn* p = P.img + base;
+          tap[m][0] = ld_val(p);
+          tap[m][1] = ld_val(p + 1);
+          tap[m][2] = ld_val(p + P.nx);
+          tap[m][3] = ld_val(p + P.nx + 1);
+          tap[m][4] = ld_val(p + P.nxy);
+          tap[m][5] = ld_val(p + P.nxy + 1);
+          tap[m][6] = ld_val(p + P.nxy + P.nx);
+          tap[m][7] = ld_val(p + P.nxy + P.nx + 1);
+        }
+        if (LAB) lab[m] = __ldg(P.lab + (base + hbx + hby * P.nx + hbz * P.nxy));
+      } else {
+        if (IMG) {
+          const bool x0 = (unsigned)fx < (unsigned)P.nx, x1 = (unsigned)(fx + 1) < (unsigned)P.nx;
+          const bool y0 = (unsigned)fy < (unsigned)P.ny, y1 = (unsigned)(fy + 1) < (unsigned)P.ny;
+          const bool z0 = (unsigned)fz < (unsigned)P.nz, z1 = (unsigned)(fz + 1) < (unsigned)P.nz;
+          // Unsigned arithmetic wraps harmlessly far outside; an index is only
+          // dereferenced when its tap lies inside the volume.
+          const unsigned ux = (unsigned)P.nx, uxy = (unsigned)P.nxy;
+          const unsigned b = ((unsigned)fz * (unsigned)P.ny + (unsigned)fy) * ux + (unsigned)fx;
+          if (x0 && y0 && z0) tap[m][0] = ld_val(P.img + b);
+          if (x1 && y0 && z0) tap[m][1] = ld_val(P.img + (b + 1u));
+          if (x0 && y1 && z0) tap[m][2] = ld_val(P.img + (b + ux));
+          if (x1 && y1 && z0) tap[m][3] = ld_val(P.img + (b + ux + 1u));
+          if (x0 && y0 && z1) tap[m][4] = ld_val(P.img + (b + uxy));
+          if (x1 && y0 && z1) tap[m][5] = ld_val(P.img + (b + uxy + 1u));
+          if (x0 && y1 && z1) tap[m][6] = ld_val(P.img + (b + uxy + ux));
+          if (x1 && y1 && z1) tap[m][7] = ld_val(P.img + (b + uxy + ux + 1u));
+        }
+        if (LAB) {
+          const int rx = fx + hbx, ry = fy + hby, rz = fz + hbz;
+          if ((unsigned)rx < (unsigned)P.nx && (unsigned)ry < (unsigned)P.ny &&
+              (unsigned)rz < (unsigned)P.nz)
+            lab[m] = __ldg(P.lab + ((rz * P.ny + ry) * P.nx + rx));
+        }
+      }
+    }
+    sx += P.dx;
+    sy += P.dy;
+    sz += P.dz;
+  }
+  float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+  if (noisy) quad_normals(quad, noise_id, key0, key1, z);
+  long long cx = s0x, cy = s0y, cz = s0z;
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
     if (m < n) {
-      fwd_voxel<TIn, MODE, IMG, LAB>(P, sx, sy, sz, z[m], o, valid);
-      sx += P.dx;
-      sy += P.dy;
-      sz += P.dz;
+      if (IMG) {
+        float v = P.fill;
+        if (MODE != MODE_EXTERIOR) {
+          const float tx = q40_frac(cx), ty = q40_frac(cy), tz = q40_frac(cz);
+          const float c00 = fmaf(tx, tap[m][1] - tap[m][0], tap[m][0]);
+          const float c10 = fmaf(tx, tap[m][3] - tap[m][2], tap[m][2]);
+          const float c01 = fmaf(tx, tap[m][5] - tap[m][4], tap[m][4]);
+          const float c11 = fmaf(tx, tap[m][7] - tap[m][6], tap[m][6]);
+          const float c0 = fmaf(ty, c10 - c00, c00);
+          const float c1 = fmaf(ty, c11 - c01, c01);
+          v = fmaf(tz, c1 - c0, c0);
+        }
+        if (valid) __stcs(P.oimg + o, fmaf(P.sigma, z[m], fmaf(P.a, v, P.b)));
+      }
+      if (LAB && valid) P.olab[o] = (uint8_t)lab[m];
+      cx += P.dx;
+      cy += P.dy;
+      cz += P.dz;
       o += P.plane;
     }
   }
@@ -132,19 +159,19 @@ __device__ __forceinline__ void fwd_tile_t(const VolConst& vc, int t, unsigned k
     const int kq = tc.k0 + 4 * q;
     if (kq >= tc.k1) break;
     const int n = min(4, tc.k1 - kq);
-    float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    if (noisy)
-      quad_normals(((unsigned long long)(kq >> 2) * ony + (unsigned)tc.jc) * onx +
-                       (unsigned)tc.ic,
-                   noise_id, key0, key1, z);
+    const unsigned long long quad =
+        ((unsigned long long)(kq >> 2) * ony + (unsigned)tc.jc) * onx + (unsigned)tc.ic;
     const long long s[3] = {sx, sy, sz};
     const int mode = warp_mode(classify_run<true>(s, ds, n - 1, P.nx, P.ny, P.nz));
     if (mode == MODE_INTERIOR)
-      fwd_quad<TIn, MODE_INTERIOR, IMG, LAB>(P, sx, sy, sz, z, o, n, tc.valid);
+      fwd_quad<TIn, MODE_INTERIOR, IMG, LAB>(P, sx, sy, sz, o, n, tc.valid, noisy, quad,
+                                             noise_id, key0, key1);
     else if (mode == MODE_EXTERIOR)
-      fwd_quad<TIn, MODE_EXTERIOR, IMG, LAB>(P, sx, sy, sz, z, o, n, tc.valid);
+      fwd_quad<TIn, MODE_EXTERIOR, IMG, LAB>(P, sx, sy, sz, o, n, tc.valid, noisy, quad,
+                                             noise_id, key0, key1);
     else
-      fwd_quad<TIn, MODE_GENERAL, IMG, LAB>(P, sx, sy, sz, z, o, n, tc.valid);
+      fwd_quad<TIn, MODE_GENERAL, IMG, LAB>(P, sx, sy, sz, o, n, tc.valid, noisy, quad,
+                                            noise_id, key0, key1);
   }
 }
 
@@ -176,19 +203,22 @@ __global__ void __launch_bounds__(NW * 32, MB)
     k_fwd_batched(const aug_volume_desc* __restrict__ descs, int n_vols, unsigned key0,
                   unsigned key1, WsHeader* ws) {
   __shared__ VolConst vc;
-  long long base = 0;
-  for (int v = 0; v < n_vols; ++v) {
-    __syncthreads();
-    stage_volume(descs + v, v, vc, ws, descs[v].out_image != nullptr, false);
-    __syncthreads();
-    if (!vc.ok) continue;
-    const int nt = tiles_in<NW, QZ>(vc.onx, vc.ony, vc.onz);
-    if (vc.out_image != nullptr || vc.out_label != nullptr) {
-      for (long long t = first_tile(base); t < nt; t += gridDim.x)
-        fwd_tile<NW, QZ>(vc, (int)t, key0, key1);
-    }
-    base += nt;
-  }
+  __shared__ aug_volume_desc raw;
+  __shared__ SchedSmem<NW * 32> sm;
+  int staged = -1;
+  for_each_tile<NW, QZ>(
+      descs, n_vols, sm,
+      [&](int c0, int cnt) {
+        validate_chunk(descs, c0, cnt, ws, NEED_IMAGE_IF_OUT, false, [](int) { return true; });
+      },
+      [&](int v, int t, long long) {
+        if (v != staged) {
+          stage_volume_fast(descs + v, v, vc, raw, NEED_IMAGE_IF_OUT, false);
+          staged = v;
+        }
+        if (vc.ok && (vc.out_image != nullptr || vc.out_label != nullptr))
+          fwd_tile<NW, QZ>(vc, t, key0, key1);
+      });
 }
 
 template <int NW, int QZ, int MB>
@@ -210,13 +240,14 @@ struct FwdVariant {
 };
 #define FWD_V(NW, QZ, MB) \
   { NW, QZ, (const void*)k_fwd_batched<NW, QZ, MB>, (const void*)k_fwd_volume<NW, QZ, MB> }
-const FwdVariant kFwd[] = {FWD_V(4, 8, 1),  FWD_V(4, 8, 12), FWD_V(8, 4, 1), FWD_V(8, 4, 6),
-                           FWD_V(4, 4, 12), FWD_V(8, 8, 6),  FWD_V(8, 2, 6), FWD_V(16, 2, 3),
-                           FWD_V(2, 8, 24)};
+const FwdVariant kFwd[] = {FWD_V(4, 8, 1), FWD_V(4, 8, 6),  FWD_V(8, 4, 1), FWD_V(8, 4, 3),
+                           FWD_V(4, 4, 6), FWD_V(8, 8, 3),  FWD_V(8, 2, 3), FWD_V(16, 2, 1),
+                           FWD_V(4, 8, 8), FWD_V(8, 4, 4)};
 #undef FWD_V
-const char* kFwdNames[] = {"tile32x4x32",       "tile32x4x32_48w", "tile32x8x16",
-                           "tile32x8x16_48w",   "tile32x4x16_48w", "tile32x8x32_48w",
-                           "tile32x8x8_48w",    "tile32x16x8_48w", "tile32x2x32_48w"};
+const char* kFwdNames[] = {"tile32x4x32",     "tile32x4x32_24w", "tile32x8x16",
+                           "tile32x8x16_24w", "tile32x4x16_24w", "tile32x8x32_24w",
+                           "tile32x8x8_24w",  "tile32x16x8",     "tile32x4x32_32w",
+                           "tile32x8x16_32w"};
 }  // namespace
 
 int fwd_num_variants() { return (int)(sizeof(kFwd) / sizeof(kFwd[0])); }

@@ -15,6 +15,7 @@
 // The warped labels never reach memory.
 #include "kernels.h"
 #include "sample.cuh"
+#include "sched.cuh"
 
 namespace augk {
 
@@ -71,23 +72,35 @@ __global__ void __launch_bounds__(NW * 32)
                const float* __restrict__ p, float* __restrict__ gp,
                const float2* __restrict__ coefs, double* partials, WsHeader* ws) {
   __shared__ IouShared<NW, C> sh;
-  long long base = 0;
-  size_t poff = 0;  // offset of this volume's [C][nvox] block
+  __shared__ aug_volume_desc raw;
+  __shared__ SchedSmem<NW * 32> sm;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  for (int v = 0; v < n_vols; ++v) {
-    __syncthreads();
-    stage_volume(descs + v, v, sh.vc, SUMS ? ws : nullptr, false, false);
-    if (SUMS && threadIdx.x < 3 * C) sh.acc[threadIdx.x] = 0.0;
-    __syncthreads();
-    const VolConst& vc = sh.vc;
-    const bool ok = vc.ok && vc.label != nullptr;
-    if (SUMS && vc.ok && vc.label == nullptr && blockIdx.x == 0 && threadIdx.x == 0)
-      record_error(ws, AUG_ERR_DESCRIPTOR, v);
-    const int nt = vc.ok ? tiles_in<NW, QZ>(vc.onx, vc.ony, vc.onz) : 0;
-    const size_t nvox = vc.ok ? (size_t)vc.onx * vc.ony * vc.onz : 0;
-    if (ok) {
-      for (long long t = first_tile(base); t < nt; t += gridDim.x) {
-        const TileCoord tc = tile_coord<NW, QZ>((int)t, vc.onx, vc.ony, vc.onz);
+  int staged = -1;
+  auto flush = [&]() {
+    if (SUMS && staged >= 0 && threadIdx.x < 3 * C)
+      partials[((size_t)blockIdx.x * n_vols + staged) * (3 * C) + threadIdx.x] =
+          sh.acc[threadIdx.x];
+  };
+  for_each_tile<NW, QZ>(
+      descs, n_vols, sm,
+      [&](int c0, int cnt) {
+        if (SUMS) {
+          validate_chunk(descs, c0, cnt, ws, NEED_IMAGE_NEVER, false,
+                         [&](int v) { return descs[v].label != nullptr; });
+          for (int i = threadIdx.x; i < cnt * 3 * C; i += blockDim.x)
+            partials[((size_t)blockIdx.x * n_vols + c0) * (3 * C) + i] = 0.0;
+        }
+      },
+      [&](int v, int t, long long voxoff) {
+        if (v != staged) {
+          flush();
+          stage_volume_fast(descs + v, v, sh.vc, raw, NEED_IMAGE_NEVER, false);
+          if (SUMS && threadIdx.x < 3 * C) sh.acc[threadIdx.x] = 0.0;
+          staged = v;
+        }
+        const VolConst& vc = sh.vc;
+        if (!vc.ok || vc.label == nullptr) return;
+        const TileCoord tc = tile_coord<NW, QZ>(t, vc.onx, vc.ony, vc.onz);
         long long s[3], ds[3];
 #pragma unroll
         for (int r = 0; r < 3; ++r) {
@@ -99,6 +112,7 @@ __global__ void __launch_bounds__(NW * 32)
         for (int m = 0; m < 3 * C; ++m) acc[m] = 0.0f;
         const int mode =
             warp_mode(classify_run<false>(s, ds, tc.k1 - 1 - tc.k0, vc.nx, vc.ny, vc.nz));
+        const size_t poff = (size_t)C * (size_t)voxoff;
         const float* pv = p + poff;
         float* gv = SUMS ? nullptr : gp + poff;
         const float2* cf = SUMS ? nullptr : coefs + (size_t)v * C;
@@ -123,13 +137,8 @@ __global__ void __launch_bounds__(NW * 32)
           }
           __syncthreads();
         }
-      }
-    }
-    if (SUMS && threadIdx.x < 3 * C)
-      partials[((size_t)blockIdx.x * n_vols + v) * (3 * C) + threadIdx.x] = sh.acc[threadIdx.x];
-    base += nt;
-    poff += (size_t)C * nvox;
-  }
+      });
+  flush();
 }
 
 // One CTA per volume: loss and the per-class gradient values.
