@@ -61,6 +61,30 @@ int persistent_grid(const void* kernel, int block, size_t smem) {
   return per_sm * sms;
 }
 
+__global__ void k_prepare(const aug_volume_desc* __restrict__ descs, int n_vols, int need,
+                          int f32_only, const float* const* gout, float* const* gin,
+                          int need_label, VolConst* __restrict__ tab, WsHeader* ws) {
+  const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  if (v >= n_vols) return;
+  const aug_volume_desc d = descs[v];
+  bool ok = desc_valid(d, needs_image(d, need), f32_only != 0);
+  if (gout != nullptr) ok &= gout[v] != nullptr;
+  if (gin != nullptr) ok &= gin[v] != nullptr;
+  if (need_label) ok &= d.label != nullptr;
+  VolConst vc;
+  make_volconst(d, ok, vc);
+  tab[v] = vc;
+  if (!ok) record_error(ws, AUG_ERR_DESCRIPTOR, v);
+}
+
+cudaError_t launch_prepare(const aug_volume_desc* d, int n, int need, bool f32_only,
+                           const float* const* gout, float* const* gin, bool need_label,
+                           VolConst* tab, WsHeader* ws, cudaStream_t st) {
+  k_prepare<<<(n + 127) / 128, 128, 0, st>>>(d, n, need, f32_only ? 1 : 0, gout, gin,
+                                              need_label ? 1 : 0, tab, ws);
+  return cudaGetLastError();
+}
+
 __global__ void k_philox(const uint32_t* __restrict__ ctr, long long n, unsigned k0,
                          unsigned k1, uint32_t* __restrict__ out) {
   for (long long m = (long long)blockIdx.x * blockDim.x + threadIdx.x; m < n;
@@ -100,11 +124,19 @@ size_t partial_bytes(int n_vols, int n_classes) {
                   sizeof(double));
 }
 
+size_t table_bytes(int n_vols) { return align256((size_t)n_vols * sizeof(VolConst)); }
+
+// Workspace: [header 256 B][per-volume constant table][per-CTA partials][class coefficients]
 size_t ws_size(int n_vols, int n_classes) {
   if (n_vols < 1 || n_vols > kMaxVols || n_classes < 0 || n_classes > kMaxClasses) return 0;
   if (device_sm_count() <= 0) return 0;
-  return sizeof(WsHeader) + partial_bytes(n_vols, n_classes) +
+  return sizeof(WsHeader) + table_bytes(n_vols) + partial_bytes(n_vols, n_classes) +
          align256((size_t)n_vols * kMaxClasses * sizeof(float2));
+}
+
+VolConst* ws_table(void* ws) { return (VolConst*)((char*)ws + sizeof(WsHeader)); }
+double* ws_partials(void* ws, int n_vols) {
+  return (double*)((char*)ws + sizeof(WsHeader) + table_bytes(n_vols));
 }
 
 aug_status check_ws(void* ws, size_t bytes, int n_vols, int n_classes) {
@@ -162,21 +194,21 @@ aug_status run_fwd(int variant, const aug_volume_desc* d, int n, uint64_t seed, 
                    cudaStream_t st) {
   unsigned k0, k1;
   split_seed(seed, &k0, &k1);
-  return from_cuda(launch_fwd_batched(variant, d, n, k0, k1, (WsHeader*)ws, st));
+  return from_cuda(launch_fwd_batched(variant, d, n, k0, k1, ws_table(ws), (WsHeader*)ws, st));
 }
 
 aug_status run_bwd(int variant, const aug_volume_desc* d, int n, const float* const* gout,
                    float* const* gin, float* gaff, void* ws, cudaStream_t st) {
-  double* partials = (double*)((char*)ws + sizeof(WsHeader));
-  return from_cuda(launch_bwd(variant, d, n, gout, gin, gaff, partials, (WsHeader*)ws, st));
+  return from_cuda(launch_bwd(variant, d, n, gout, gin, gaff, ws_table(ws), ws_partials(ws, n),
+                              (WsHeader*)ws, st));
 }
 
 aug_status run_iou(int variant, const aug_volume_desc* d, int n, const float* p, int C,
                    float* loss, float* gp, void* ws, cudaStream_t st) {
-  double* partials = (double*)((char*)ws + sizeof(WsHeader));
-  float2* coefs = (float2*)((char*)ws + sizeof(WsHeader) + partial_bytes(n, C));
-  return from_cuda(
-      launch_iou(variant, d, n, p, C, loss, gp, partials, coefs, (WsHeader*)ws, st));
+  double* partials = ws_partials(ws, n);
+  float2* coefs = (float2*)((char*)partials + partial_bytes(n, C));
+  return from_cuda(launch_iou(variant, d, n, p, C, loss, gp, ws_table(ws), partials, coefs,
+                              (WsHeader*)ws, st));
 }
 
 }  // namespace

@@ -94,14 +94,13 @@ __device__ __forceinline__ void bwd_run(const VolConst& vc, const TileCoord& tc,
 
 template <int NW>
 struct BwdShared {
-  VolConst vc;
   float red[NW][12];
   double acc[12];
 };
 
 template <typename TIn, int NW, int QZ, bool GIN, bool GT>
-__device__ __forceinline__ void bwd_tile(BwdShared<NW>& sh, int t, const float* g, float* gin) {
-  const VolConst& vc = sh.vc;
+__device__ __forceinline__ void bwd_tile(const VolConst& vc, BwdShared<NW>& sh, int t,
+                                         const float* g, float* gin) {
   const TileCoord tc = tile_coord<NW, QZ>(t, vc.onx, vc.ony, vc.onz);
   long long s[3], ds[3];
 #pragma unroll
@@ -147,45 +146,41 @@ __device__ __forceinline__ void bwd_tile(BwdShared<NW>& sh, int t, const float* 
 template <int NW, int QZ, bool GIN, bool GT>
 __global__ void __launch_bounds__(NW * 32)
     k_bwd_batched(const aug_volume_desc* __restrict__ descs, int n_vols,
-                  const float* const* gout, float* const* gin, double* partials, WsHeader* ws) {
+                  const VolConst* __restrict__ tab, const float* const* gout,
+                  float* const* gin, double* partials) {
   __shared__ BwdShared<NW> sh;
-  __shared__ aug_volume_desc raw;
   __shared__ SchedSmem<NW * 32> sm;
   int staged = -1;
-  const float* g = nullptr;
-  float* gi = nullptr;
+  // Threads 0..11 own sh.acc[0..11]: they zero, accumulate and flush it, so
+  // the flush needs no barrier.
   auto flush = [&]() {
-    // Each of threads 0..11 wrote its own sh.acc entry: no barrier needed.
     if (GT && staged >= 0 && threadIdx.x < 12)
       partials[((size_t)blockIdx.x * n_vols + staged) * 12 + threadIdx.x] = sh.acc[threadIdx.x];
   };
   for_each_tile<NW, QZ>(
       descs, n_vols, sm,
       [&](int c0, int cnt) {
-        validate_chunk(descs, c0, cnt, ws, NEED_IMAGE_ALWAYS, GIN, [&](int v) {
-          return gout[v] != nullptr && (!GIN || gin[v] != nullptr);
-        });
         // This CTA's partials of the chunk's volumes start at zero (volumes in
         // which it has no tile keep them).
         if (GT)
           for (int i = threadIdx.x; i < cnt * 12; i += blockDim.x)
             partials[((size_t)blockIdx.x * n_vols + c0) * 12 + i] = 0.0;
+        __syncthreads();
       },
       [&](int v, int t, long long) {
         if (v != staged) {
           flush();
-          stage_volume_fast(descs + v, v, sh.vc, raw, NEED_IMAGE_ALWAYS, GIN);
-          if (threadIdx.x < 12) sh.acc[threadIdx.x] = 0.0;
+          if (GT && threadIdx.x < 12) sh.acc[threadIdx.x] = 0.0;
           staged = v;
-          g = gout[v];
-          gi = GIN ? gin[v] : nullptr;
         }
-        if (sh.vc.ok && g != nullptr && (!GIN || gi != nullptr)) {
-          if (sh.vc.dtype == AUG_I16)
-            bwd_tile<int16_t, NW, QZ, GIN, GT>(sh, t, g, gi);
-          else
-            bwd_tile<float, NW, QZ, GIN, GT>(sh, t, g, gi);
-        }
+        const VolConst& vc = tab[v];
+        if (!vc.ok) return;
+        const float* g = gout[v];
+        float* gi = GIN ? gin[v] : nullptr;
+        if (vc.dtype == AUG_I16)
+          bwd_tile<int16_t, NW, QZ, GIN, GT>(vc, sh, t, g, gi);
+        else
+          bwd_tile<float, NW, QZ, GIN, GT>(vc, sh, t, g, gi);
       });
   flush();
 }
@@ -252,12 +247,13 @@ int bwd_num_variants() { return (int)(sizeof(kBwd) / sizeof(kBwd[0])); }
 const char* bwd_variant_name(int v) { return kBwdNames[v]; }
 
 cudaError_t launch_bwd(int variant, const aug_volume_desc* d, int n, const float* const* gout,
-                       float* const* gin, float* gaff, double* partials, WsHeader* ws,
-                       cudaStream_t st) {
+                       float* const* gin, float* gaff, VolConst* tab, double* partials,
+                       WsHeader* ws, cudaStream_t st) {
   const BwdVariant& bv = kBwd[variant];
   const bool want_gin = gin != nullptr, want_gt = gaff != nullptr;
   if (!want_gin && !want_gt) return cudaSuccess;
-  cudaError_t e;
+  cudaError_t e = launch_prepare(d, n, NEED_IMAGE_ALWAYS, want_gin, gout, gin, false, tab, ws, st);
+  if (e != cudaSuccess) return e;
   if (want_gin) {
     const int zgrid = persistent_grid((const void*)k_zero_grad_in, 256, 0);
     if (zgrid <= 0) return cudaErrorInvalidConfiguration;
@@ -268,7 +264,8 @@ cudaError_t launch_bwd(int variant, const aug_volume_desc* d, int n, const float
   const int block = bv.nw * 32;
   const int grid = persistent_grid(kern, block, 0);
   if (grid <= 0) return cudaErrorInvalidConfiguration;
-  void* args[] = {(void*)&d, (void*)&n, (void*)&gout, (void*)&gin, (void*)&partials, (void*)&ws};
+  const VolConst* ctab = tab;
+  void* args[] = {(void*)&d, (void*)&n, (void*)&ctab, (void*)&gout, (void*)&gin, (void*)&partials};
   if ((e = cudaLaunchKernel(kern, dim3(grid), dim3(block), args, 0, st)) != cudaSuccess) return e;
   if (want_gt) {
     k_bwd_finalize<<<n, 384, 0, st>>>(partials, grid, n, gaff);

@@ -73,42 +73,33 @@ __device__ inline bool desc_valid(const aug_volume_desc& d, bool need_image, boo
   return ok;
 }
 
-// Parses a descriptor into per-volume constants (threads 0..11 convert the
-// affine to Q.40, thread 0 the rest).  The caller synchronises afterwards.
-// Errors are recorded by the caller's validation pass, not here.
-__device__ inline void stage_volume(const aug_volume_desc* __restrict__ d, int v, VolConst& vc,
-                                    WsHeader* ws, bool need_image, bool f32_only) {
-  if (threadIdx.x < 12) {
-    const int r = threadIdx.x >> 2, c = threadIdx.x & 3;
-    const float t = d->affine[threadIdx.x];
-    const float lim = (c < 3) ? 64.0f : 1048576.0f;
-    long long q = 0;
-    if (isfinite(t) && fabsf(t) <= lim) q = __double2ll_rn((double)t * 1099511627776.0);
-    vc.tq[r][c] = q;
+// Parses one descriptor into per-volume constants (one thread).
+__device__ inline void make_volconst(const aug_volume_desc& d, bool ok, VolConst& vc) {
+#pragma unroll
+  for (int m = 0; m < 12; ++m) {
+    const float t = d.affine[m];
+    const float lim = ((m & 3) < 3) ? 64.0f : 1048576.0f;
+    vc.tq[m >> 2][m & 3] =
+        (isfinite(t) && fabsf(t) <= lim) ? __double2ll_rn((double)t * 1099511627776.0) : 0LL;
   }
-  if (threadIdx.x == 0) {
-    vc.image = d->image;
-    vc.label = d->label;
-    vc.out_image = d->out_image;
-    vc.out_label = d->out_label;
-    vc.nx = d->in_nx;
-    vc.ny = d->in_ny;
-    vc.nz = d->in_nz;
-    vc.dtype = d->image_dtype;
-    vc.onx = d->out_nx;
-    vc.ony = d->out_ny;
-    vc.onz = d->out_nz;
-    vc.fill_label = d->fill_label;
-    vc.a = d->photo_a;
-    vc.b = d->photo_b;
-    vc.sigma = d->noise_sigma;
-    vc.fill = d->fill_image;
-    vc.noise_id = d->noise_id;
-    const bool ok = desc_valid(*d, need_image, f32_only);
-    vc.ok = ok ? 1 : 0;
-    // Kernels without a validation pass (one volume per launch) record here.
-    if (!ok && ws != nullptr && blockIdx.x == 0) record_error(ws, AUG_ERR_DESCRIPTOR, v);
-  }
+  vc.image = d.image;
+  vc.label = d.label;
+  vc.out_image = d.out_image;
+  vc.out_label = d.out_label;
+  vc.nx = d.in_nx;
+  vc.ny = d.in_ny;
+  vc.nz = d.in_nz;
+  vc.dtype = d.image_dtype;
+  vc.onx = d.out_nx;
+  vc.ony = d.out_ny;
+  vc.onz = d.out_nz;
+  vc.fill_label = d.fill_label;
+  vc.a = d.photo_a;
+  vc.b = d.photo_b;
+  vc.sigma = d.noise_sigma;
+  vc.fill = d.fill_image;
+  vc.noise_id = d.noise_id;
+  vc.ok = ok ? 1 : 0;
 }
 
 // ---- Q.40 coordinate helpers ------------------------------------------------

@@ -200,22 +200,13 @@ __device__ __forceinline__ void fwd_tile(const VolConst& vc, int t, unsigned key
 // (1 = no constraint); part of the variant, chosen by measurement.
 template <int NW, int QZ, int MB>
 __global__ void __launch_bounds__(NW * 32, MB)
-    k_fwd_batched(const aug_volume_desc* __restrict__ descs, int n_vols, unsigned key0,
-                  unsigned key1, WsHeader* ws) {
-  __shared__ VolConst vc;
-  __shared__ aug_volume_desc raw;
+    k_fwd_batched(const aug_volume_desc* __restrict__ descs, int n_vols,
+                  const VolConst* __restrict__ tab, unsigned key0, unsigned key1) {
   __shared__ SchedSmem<NW * 32> sm;
-  int staged = -1;
   for_each_tile<NW, QZ>(
-      descs, n_vols, sm,
-      [&](int c0, int cnt) {
-        validate_chunk(descs, c0, cnt, ws, NEED_IMAGE_IF_OUT, false, [](int) { return true; });
-      },
+      descs, n_vols, sm, [](int, int) {},
       [&](int v, int t, long long) {
-        if (v != staged) {
-          stage_volume_fast(descs + v, v, vc, raw, NEED_IMAGE_IF_OUT, false);
-          staged = v;
-        }
+        const VolConst& vc = tab[v];
         if (vc.ok && (vc.out_image != nullptr || vc.out_label != nullptr))
           fwd_tile<NW, QZ>(vc, t, key0, key1);
       });
@@ -225,7 +216,7 @@ template <int NW, int QZ, int MB>
 __global__ void __launch_bounds__(NW * 32, MB)
     k_fwd_volume(const aug_volume_desc desc, unsigned key0, unsigned key1) {
   __shared__ VolConst vc;
-  stage_volume(&desc, 0, vc, nullptr, desc.out_image != nullptr, false);
+  if (threadIdx.x == 0) make_volconst(desc, desc_valid(desc, desc.out_image != nullptr, false), vc);
   __syncthreads();
   if (!vc.ok) return;
   fwd_tile<NW, QZ>(vc, blockIdx.x, key0, key1);
@@ -254,12 +245,16 @@ int fwd_num_variants() { return (int)(sizeof(kFwd) / sizeof(kFwd[0])); }
 const char* fwd_variant_name(int v) { return kFwdNames[v]; }
 
 cudaError_t launch_fwd_batched(int variant, const aug_volume_desc* d, int n, unsigned k0,
-                               unsigned k1, WsHeader* ws, cudaStream_t st) {
+                               unsigned k1, VolConst* tab, WsHeader* ws, cudaStream_t st) {
   const FwdVariant& fv = kFwd[variant];
   const int block = fv.nw * 32;
   const int grid = persistent_grid(fv.batched, block, 0);
   if (grid <= 0) return cudaErrorInvalidConfiguration;
-  void* args[] = {(void*)&d, (void*)&n, (void*)&k0, (void*)&k1, (void*)&ws};
+  cudaError_t e = launch_prepare(d, n, NEED_IMAGE_IF_OUT, false, nullptr, nullptr, false, tab, ws,
+                                 st);
+  if (e != cudaSuccess) return e;
+  const VolConst* ctab = tab;
+  void* args[] = {(void*)&d, (void*)&n, (void*)&ctab, (void*)&k0, (void*)&k1};
   return cudaLaunchKernel(fv.batched, dim3(grid), dim3(block), args, 0, st);
 }
 

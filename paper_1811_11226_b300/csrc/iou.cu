@@ -61,7 +61,6 @@ __device__ __forceinline__ void iou_run(const VolConst& vc, const TileCoord& tc,
 
 template <int NW, int C>
 struct IouShared {
-  VolConst vc;
   float red[NW][3 * C];
   double acc[3 * C];
 };
@@ -69,13 +68,13 @@ struct IouShared {
 template <int NW, int QZ, int C, bool SUMS>
 __global__ void __launch_bounds__(NW * 32)
     k_iou_pass(const aug_volume_desc* __restrict__ descs, int n_vols,
-               const float* __restrict__ p, float* __restrict__ gp,
-               const float2* __restrict__ coefs, double* partials, WsHeader* ws) {
+               const VolConst* __restrict__ tab, const float* __restrict__ p,
+               float* __restrict__ gp, const float2* __restrict__ coefs, double* partials) {
   __shared__ IouShared<NW, C> sh;
-  __shared__ aug_volume_desc raw;
   __shared__ SchedSmem<NW * 32> sm;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int staged = -1;
+  // Threads 0..3C-1 own sh.acc: they zero, accumulate and flush it.
   auto flush = [&]() {
     if (SUMS && staged >= 0 && threadIdx.x < 3 * C)
       partials[((size_t)blockIdx.x * n_vols + staged) * (3 * C) + threadIdx.x] =
@@ -85,21 +84,19 @@ __global__ void __launch_bounds__(NW * 32)
       descs, n_vols, sm,
       [&](int c0, int cnt) {
         if (SUMS) {
-          validate_chunk(descs, c0, cnt, ws, NEED_IMAGE_NEVER, false,
-                         [&](int v) { return descs[v].label != nullptr; });
           for (int i = threadIdx.x; i < cnt * 3 * C; i += blockDim.x)
             partials[((size_t)blockIdx.x * n_vols + c0) * (3 * C) + i] = 0.0;
+          __syncthreads();
         }
       },
       [&](int v, int t, long long voxoff) {
         if (v != staged) {
           flush();
-          stage_volume_fast(descs + v, v, sh.vc, raw, NEED_IMAGE_NEVER, false);
           if (SUMS && threadIdx.x < 3 * C) sh.acc[threadIdx.x] = 0.0;
           staged = v;
         }
-        const VolConst& vc = sh.vc;
-        if (!vc.ok || vc.label == nullptr) return;
+        const VolConst& vc = tab[v];
+        if (!vc.ok) return;
         const TileCoord tc = tile_coord<NW, QZ>(t, vc.onx, vc.ony, vc.onz);
         long long s[3], ds[3];
 #pragma unroll
@@ -207,18 +204,22 @@ int iou_num_variants() { return (int)(sizeof(kIou) / sizeof(kIou[0])); }
 const char* iou_variant_name(int v) { return kIouNames[v]; }
 
 cudaError_t launch_iou(int variant, const aug_volume_desc* d, int n, const float* p, int C,
-                       float* loss, float* gp, double* partials, float2* coefs, WsHeader* ws,
-                       cudaStream_t st) {
+                       float* loss, float* gp, VolConst* tab, double* partials, float2* coefs,
+                       WsHeader* ws, cudaStream_t st) {
   const IouVariant& iv = kIou[variant];
   const int block = iv.nw * 32;
   const void* ks = iv.sums[C - 1];
   const int grid = persistent_grid(ks, block, 0);
   if (grid <= 0) return cudaErrorInvalidConfiguration;
+  cudaError_t e = launch_prepare(d, n, NEED_IMAGE_NEVER, false, nullptr, nullptr, true, tab, ws,
+                                 st);
+  if (e != cudaSuccess) return e;
   float* null_f = nullptr;
   const float2* cnull = nullptr;
-  void* a1[] = {(void*)&d,     (void*)&n,        (void*)&p, (void*)&null_f,
-                (void*)&cnull, (void*)&partials, (void*)&ws};
-  cudaError_t e = cudaLaunchKernel(ks, dim3(grid), dim3(block), a1, 0, st);
+  const VolConst* ctab = tab;
+  void* a1[] = {(void*)&d,     (void*)&n,     (void*)&ctab,     (void*)&p,
+                (void*)&null_f, (void*)&cnull, (void*)&partials};
+  e = cudaLaunchKernel(ks, dim3(grid), dim3(block), a1, 0, st);
   if (e != cudaSuccess) return e;
   float2* cf = gp ? coefs : nullptr;
   int n_ctas = grid;

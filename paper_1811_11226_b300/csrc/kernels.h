@@ -6,6 +6,7 @@
 
 #include "augwarp.h"
 #include "common.cuh"
+#include "sched.cuh"
 
 namespace augk {
 
@@ -17,22 +18,27 @@ int device_sm_count();
 
 int fwd_num_variants();
 const char* fwd_variant_name(int v);
+// Prologue of each batched call (k_prepare): per-volume constant table.
+cudaError_t launch_prepare(const aug_volume_desc* d, int n, int need, bool f32_only,
+                           const float* const* gout, float* const* gin, bool need_label,
+                           VolConst* tab, WsHeader* ws, cudaStream_t st);
+
 cudaError_t launch_fwd_batched(int variant, const aug_volume_desc* d, int n, unsigned k0,
-                               unsigned k1, WsHeader* ws, cudaStream_t st);
+                               unsigned k1, VolConst* tab, WsHeader* ws, cudaStream_t st);
 cudaError_t launch_fwd_volume(int variant, const aug_volume_desc& h, unsigned k0, unsigned k1,
                               cudaStream_t st);
 
 int bwd_num_variants();
 const char* bwd_variant_name(int v);
 cudaError_t launch_bwd(int variant, const aug_volume_desc* d, int n, const float* const* gout,
-                       float* const* gin, float* gaff, double* partials, WsHeader* ws,
-                       cudaStream_t st);
+                       float* const* gin, float* gaff, VolConst* tab, double* partials,
+                       WsHeader* ws, cudaStream_t st);
 
 int iou_num_variants();
 const char* iou_variant_name(int v);
 cudaError_t launch_iou(int variant, const aug_volume_desc* d, int n, const float* p, int C,
-                       float* loss, float* gp, double* partials, float2* coefs, WsHeader* ws,
-                       cudaStream_t st);
+                       float* loss, float* gp, VolConst* tab, double* partials, float2* coefs,
+                       WsHeader* ws, cudaStream_t st);
 
 cudaError_t launch_philox(const uint32_t* ctr, long long n, unsigned k0, unsigned k1,
                           uint32_t* out, cudaStream_t st);

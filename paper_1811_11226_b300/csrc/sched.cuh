@@ -107,32 +107,13 @@ __device__ __forceinline__ bool needs_image(const aug_volume_desc& d, int need) 
   return need == NEED_IMAGE_ALWAYS || (need == NEED_IMAGE_IF_OUT && d.out_image != nullptr);
 }
 
-// CTA 0 checks every descriptor of a chunk (one per thread) and records the
-// first invalid one in the workspace status word.  extra(v) adds per-kernel
-// checks (buffer pointers).
-template <typename ExtraF>
-__device__ __forceinline__ void validate_chunk(const aug_volume_desc* __restrict__ descs, int c0,
-                                               int cnt, WsHeader* ws, int need, bool f32_only,
-                                               ExtraF&& extra) {
-  if (blockIdx.x != 0 || (int)threadIdx.x >= cnt) return;
-  const int v = c0 + threadIdx.x;
-  const aug_volume_desc& d = descs[v];
-  if (!desc_valid(d, needs_image(d, need), f32_only) || !extra(v))
-    record_error(ws, AUG_ERR_DESCRIPTOR, v);
-}
-
-// Copies a descriptor into shared memory with one coalesced read (36 words),
-// then parses it.  All threads call it; it synchronises.
-__device__ inline void stage_volume_fast(const aug_volume_desc* __restrict__ d, int v,
-                                         VolConst& vc, aug_volume_desc& raw, int need,
-                                         bool f32_only) {
-  __syncthreads();  // previous users of vc / raw are done
-  if (threadIdx.x < sizeof(aug_volume_desc) / 4)
-    reinterpret_cast<unsigned*>(&raw)[threadIdx.x] =
-        __ldg(reinterpret_cast<const unsigned*>(d) + threadIdx.x);
-  __syncthreads();
-  stage_volume(&raw, v, vc, nullptr, needs_image(raw, need), f32_only);
-  __syncthreads();
-}
+// Prologue of every batched call, one thread per volume: validates the
+// descriptor (plus the per-op buffer pointers), records the first invalid one
+// in the workspace status word, and writes the parsed per-volume constants
+// (affine in Q.40, ok flag) to a table in the workspace.  The main kernels
+// read a tile's constants straight from that table (L1-cached, no barrier).
+__global__ void k_prepare(const aug_volume_desc* __restrict__ descs, int n_vols, int need,
+                          int f32_only, const float* const* gout, float* const* gin,
+                          int need_label, VolConst* __restrict__ tab, WsHeader* ws);
 
 }  // namespace augk
