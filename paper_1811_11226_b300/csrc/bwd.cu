@@ -225,17 +225,17 @@ __global__ void k_bwd_finalize(const double* __restrict__ partials, int n_ctas, 
 
 // ---- host launchers ------------------------------------------------------------
 namespace {
+using BwdK = void (*)(const aug_volume_desc*, int, const VolConst*, const float* const*,
+                      float* const*, double*);
 struct BwdVariant {
   int nw, qz;
-  const void* k[4];  // [GIN*2 + GT]
+  BwdK k[4];  // [GIN*2 + GT]
 };
-#define BWD_V(NW, QZ)                                                               \
-  {                                                                                 \
-    NW, QZ,                                                                         \
-        {(const void*)k_bwd_batched<NW, QZ, false, false>,                          \
-         (const void*)k_bwd_batched<NW, QZ, false, true>,                           \
-         (const void*)k_bwd_batched<NW, QZ, true, false>,                           \
-         (const void*)k_bwd_batched<NW, QZ, true, true> }                           \
+#define BWD_V(NW, QZ)                                                                  \
+  {                                                                                    \
+    NW, QZ,                                                                            \
+        {k_bwd_batched<NW, QZ, false, false>, k_bwd_batched<NW, QZ, false, true>,      \
+         k_bwd_batched<NW, QZ, true, false>, k_bwd_batched<NW, QZ, true, true> }       \
   }
 const BwdVariant kBwd[] = {BWD_V(8, 4), BWD_V(4, 4), BWD_V(8, 2), BWD_V(8, 8), BWD_V(4, 8)};
 #undef BWD_V
@@ -252,7 +252,8 @@ cudaError_t launch_bwd(int variant, const aug_volume_desc* d, int n, const float
   const BwdVariant& bv = kBwd[variant];
   const bool want_gin = gin != nullptr, want_gt = gaff != nullptr;
   if (!want_gin && !want_gt) return cudaSuccess;
-  cudaError_t e = launch_prepare(d, n, NEED_IMAGE_ALWAYS, want_gin, gout, gin, false, tab, ws, st);
+  cudaError_t e =
+      launch_prepare(d, n, NEED_IMAGE_ALWAYS, want_gin, gout, gin, false, tab, ws, st);
   if (e != cudaSuccess) return e;
   if (want_gin) {
     const int zgrid = persistent_grid((const void*)k_zero_grad_in, 256, 0);
@@ -260,13 +261,12 @@ cudaError_t launch_bwd(int variant, const aug_volume_desc* d, int n, const float
     k_zero_grad_in<<<zgrid, 256, 0, st>>>(d, n, gin);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  const void* kern = bv.k[(want_gin ? 2 : 0) + (want_gt ? 1 : 0)];
+  const BwdK kern = bv.k[(want_gin ? 2 : 0) + (want_gt ? 1 : 0)];
   const int block = bv.nw * 32;
-  const int grid = persistent_grid(kern, block, 0);
+  const int grid = persistent_grid((const void*)kern, block, 0);
   if (grid <= 0) return cudaErrorInvalidConfiguration;
-  const VolConst* ctab = tab;
-  void* args[] = {(void*)&d, (void*)&n, (void*)&ctab, (void*)&gout, (void*)&gin, (void*)&partials};
-  if ((e = cudaLaunchKernel(kern, dim3(grid), dim3(block), args, 0, st)) != cudaSuccess) return e;
+  kern<<<grid, block, 0, st>>>(d, n, tab, gout, gin, partials);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (want_gt) {
     k_bwd_finalize<<<n, 384, 0, st>>>(partials, grid, n, gaff);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

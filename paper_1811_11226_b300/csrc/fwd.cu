@@ -224,13 +224,15 @@ __global__ void __launch_bounds__(NW * 32, MB)
 
 // ---- host launchers ----------------------------------------------------------
 namespace {
+using FwdBK = void (*)(const aug_volume_desc*, int, const VolConst*, unsigned, unsigned);
+using FwdVK = void (*)(const aug_volume_desc, unsigned, unsigned);
 struct FwdVariant {
   int nw, qz;
-  const void* batched;
-  const void* volume;
+  FwdBK batched;
+  FwdVK volume;
 };
 #define FWD_V(NW, QZ, MB) \
-  { NW, QZ, (const void*)k_fwd_batched<NW, QZ, MB>, (const void*)k_fwd_volume<NW, QZ, MB> }
+  { NW, QZ, k_fwd_batched<NW, QZ, MB>, k_fwd_volume<NW, QZ, MB> }
 const FwdVariant kFwd[] = {FWD_V(4, 8, 1), FWD_V(4, 8, 6),  FWD_V(8, 4, 1), FWD_V(8, 4, 3),
                            FWD_V(4, 4, 6), FWD_V(8, 8, 3),  FWD_V(8, 2, 3), FWD_V(16, 2, 1),
                            FWD_V(4, 8, 8), FWD_V(8, 4, 4)};
@@ -248,14 +250,13 @@ cudaError_t launch_fwd_batched(int variant, const aug_volume_desc* d, int n, uns
                                unsigned k1, VolConst* tab, WsHeader* ws, cudaStream_t st) {
   const FwdVariant& fv = kFwd[variant];
   const int block = fv.nw * 32;
-  const int grid = persistent_grid(fv.batched, block, 0);
+  const int grid = persistent_grid((const void*)fv.batched, block, 0);
   if (grid <= 0) return cudaErrorInvalidConfiguration;
   cudaError_t e = launch_prepare(d, n, NEED_IMAGE_IF_OUT, false, nullptr, nullptr, false, tab, ws,
                                  st);
   if (e != cudaSuccess) return e;
-  const VolConst* ctab = tab;
-  void* args[] = {(void*)&d, (void*)&n, (void*)&ctab, (void*)&k0, (void*)&k1};
-  return cudaLaunchKernel(fv.batched, dim3(grid), dim3(block), args, 0, st);
+  fv.batched<<<grid, block, 0, st>>>(d, n, tab, k0, k1);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_fwd_volume(int variant, const aug_volume_desc& h, unsigned k0, unsigned k1,
@@ -265,9 +266,8 @@ cudaError_t launch_fwd_volume(int variant, const aug_volume_desc& h, unsigned k0
                           ((h.out_ny + fv.nw - 1) / fv.nw) *
                           ((h.out_nz + 4 * fv.qz - 1) / (4 * fv.qz));
   if (tiles <= 0 || tiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  aug_volume_desc copy = h;
-  void* args[] = {(void*)&copy, (void*)&k0, (void*)&k1};
-  return cudaLaunchKernel(fv.volume, dim3((unsigned)tiles), dim3(fv.nw * 32), args, 0, st);
+  fv.volume<<<(unsigned)tiles, fv.nw * 32, 0, st>>>(h, k0, k1);
+  return cudaGetLastError();
 }
 
 }  // namespace augk

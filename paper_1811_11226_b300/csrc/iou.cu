@@ -175,28 +175,28 @@ __global__ void k_iou_finalize(const double* __restrict__ partials, int n_ctas, 
 
 // ---- host launchers ----------------------------------------------------------------
 namespace {
+using PassK = void (*)(const aug_volume_desc*, int, const VolConst*, const float*, float*,
+                       const float2*, double*);
+using FinK = void (*)(const double*, int, int, float*, float2*);
 struct IouVariant {
   int nw, qz;
-  const void* sums[8];
-  const void* grad[8];
+  PassK sums[8];
+  PassK grad[8];
 };
-#define IOU_K(NW, QZ, S)                                                          \
-  {                                                                               \
-    (const void*)k_iou_pass<NW, QZ, 1, S>, (const void*)k_iou_pass<NW, QZ, 2, S>, \
-        (const void*)k_iou_pass<NW, QZ, 3, S>, (const void*)k_iou_pass<NW, QZ, 4, S>, \
-        (const void*)k_iou_pass<NW, QZ, 5, S>, (const void*)k_iou_pass<NW, QZ, 6, S>, \
-        (const void*)k_iou_pass<NW, QZ, 7, S>, (const void*)k_iou_pass<NW, QZ, 8, S>  \
+#define IOU_K(NW, QZ, S)                                                                 \
+  {                                                                                      \
+    k_iou_pass<NW, QZ, 1, S>, k_iou_pass<NW, QZ, 2, S>, k_iou_pass<NW, QZ, 3, S>,        \
+        k_iou_pass<NW, QZ, 4, S>, k_iou_pass<NW, QZ, 5, S>, k_iou_pass<NW, QZ, 6, S>,    \
+        k_iou_pass<NW, QZ, 7, S>, k_iou_pass<NW, QZ, 8, S>                               \
   }
 #define IOU_V(NW, QZ) \
   { NW, QZ, IOU_K(NW, QZ, true), IOU_K(NW, QZ, false) }
 const IouVariant kIou[] = {IOU_V(8, 4), IOU_V(4, 4), IOU_V(8, 8), IOU_V(4, 8)};
 #undef IOU_V
 #undef IOU_K
-const void* kIouFin[8] = {
-    (const void*)k_iou_finalize<1>, (const void*)k_iou_finalize<2>,
-    (const void*)k_iou_finalize<3>, (const void*)k_iou_finalize<4>,
-    (const void*)k_iou_finalize<5>, (const void*)k_iou_finalize<6>,
-    (const void*)k_iou_finalize<7>, (const void*)k_iou_finalize<8>};
+const FinK kIouFin[8] = {k_iou_finalize<1>, k_iou_finalize<2>, k_iou_finalize<3>,
+                         k_iou_finalize<4>, k_iou_finalize<5>, k_iou_finalize<6>,
+                         k_iou_finalize<7>, k_iou_finalize<8>};
 const char* kIouNames[] = {"tile32x8x16", "tile32x4x16", "tile32x8x32", "tile32x4x32"};
 }  // namespace
 
@@ -208,33 +208,22 @@ cudaError_t launch_iou(int variant, const aug_volume_desc* d, int n, const float
                        WsHeader* ws, cudaStream_t st) {
   const IouVariant& iv = kIou[variant];
   const int block = iv.nw * 32;
-  const void* ks = iv.sums[C - 1];
-  const int grid = persistent_grid(ks, block, 0);
+  const PassK ks = iv.sums[C - 1];
+  const int grid = persistent_grid((const void*)ks, block, 0);
   if (grid <= 0) return cudaErrorInvalidConfiguration;
   cudaError_t e = launch_prepare(d, n, NEED_IMAGE_NEVER, false, nullptr, nullptr, true, tab, ws,
                                  st);
   if (e != cudaSuccess) return e;
-  float* null_f = nullptr;
-  const float2* cnull = nullptr;
-  const VolConst* ctab = tab;
-  void* a1[] = {(void*)&d,     (void*)&n,     (void*)&ctab,     (void*)&p,
-                (void*)&null_f, (void*)&cnull, (void*)&partials};
-  e = cudaLaunchKernel(ks, dim3(grid), dim3(block), a1, 0, st);
-  if (e != cudaSuccess) return e;
-  float2* cf = gp ? coefs : nullptr;
-  int n_ctas = grid;
-  void* af[] = {(void*)&partials, (void*)&n_ctas, (void*)&n, (void*)&loss, (void*)&cf};
-  if ((e = cudaLaunchKernel(kIouFin[C - 1], dim3(n), dim3(256), af, 0, st)) != cudaSuccess)
-    return e;
+  ks<<<grid, block, 0, st>>>(d, n, tab, p, nullptr, nullptr, partials);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  kIouFin[C - 1]<<<n, 256, 0, st>>>(partials, grid, n, loss, gp ? coefs : nullptr);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (gp) {
-    const void* kg = iv.grad[C - 1];
-    const int g2 = persistent_grid(kg, block, 0);
+    const PassK kg = iv.grad[C - 1];
+    const int g2 = persistent_grid((const void*)kg, block, 0);
     if (g2 <= 0) return cudaErrorInvalidConfiguration;
-    const float2* ccf = coefs;
-    double* pnull = nullptr;
-    void* a2[] = {(void*)&d, (void*)&n, (void*)&p, (void*)&gp, (void*)&ccf, (void*)&pnull,
-                  (void*)&ws};
-    if ((e = cudaLaunchKernel(kg, dim3(g2), dim3(block), a2, 0, st)) != cudaSuccess) return e;
+    kg<<<g2, block, 0, st>>>(d, n, tab, p, gp, coefs, nullptr);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
