@@ -173,9 +173,9 @@ __device__ __forceinline__ float cos_approx(float x) {
 // R = sqrt(-2 ln u1).
 //
 // -2 ln u1: for v = 1 - u1 < 2^-6 (exact in float) the series
-// 2 v (1 + v/2 + v^2/3 + v^3/4) (Taylor series of -2 ln(1 - v), relative
-// truncation error < v^4/5 < 2e-8) keeps full relative accuracy where R is
-// small; otherwise -2 ln 2 * log2(u1) with the hardware log2 (absolute error
+// 2 v (1 + v/2 + v^2/3) (Taylor series of -2 ln(1 - v), relative truncation
+// error < v^3/2 < 2e-6, i.e. < 2e-7 absolute on R <= 0.18) keeps full
+// accuracy where R is small; otherwise -2 ln 2 * log2(u1) with the hardware log2 (absolute error
 // ~2^-22), which changes R by < 1e-6 there since R > 0.17.  R uses the
 // hardware square root (relative error ~2^-23).  The angle is
 // a = 2 pi u2 - pi in [-pi, pi), where the hardware sine/cosine have absolute
@@ -184,9 +184,8 @@ __device__ __forceinline__ float cos_approx(float x) {
 __device__ __forceinline__ float2 box_muller(unsigned ra, unsigned rb) {
   const unsigned m1 = ra >> 8, m2 = rb >> 8;
   const float u1 = (float)(m1 + 1u) * 5.9604644775390625e-8f;
-  const float v = (float)(0xFFFFFFu - m1) * 5.9604644775390625e-8f;  // 1 - u1, exact
-  const float series =
-      2.0f * v * fmaf(v, fmaf(v, fmaf(v, 0.25f, 0.333333333f), 0.5f), 1.0f);
+  const float v = 1.0f - u1;  // exact: u1 lies on the 2^-24 grid of (0, 1]
+  const float series = 2.0f * v * fmaf(v, fmaf(v, 0.333333333f, 0.5f), 1.0f);
   const float x = (v < 0.015625f) ? series : -1.38629436112f * lg2_approx(u1);
   const float r = sqrt_approx(x);
   const float a = fmaf((float)m2 * 5.9604644775390625e-8f, 6.28318530718f, -3.14159265359f);

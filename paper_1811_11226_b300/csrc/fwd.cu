@@ -28,103 +28,130 @@ struct FwdP {
   uint8_t* olab;
   long long dx, dy, dz;
   int nx, ny, nz, nxy, plane, fill_label;
-  float a, b, sigma, fill;
+  float a, b, sigma, fill, yfill;  // yfill = a * fill + b
 };
 
-// One quad (n = 1..4 z-consecutive voxels) for a warp-uniform MODE,
-// software-pipelined: every tap and label load of the quad is issued first,
-// the quad's Philox + Box-Muller normals are computed while they are in
-// flight, and only then are the samples interpolated and stored.
-template <typename TIn, int MODE, bool IMG, bool LAB>
-__device__ __forceinline__ void fwd_quad(const FwdP<TIn>& P, long long& sx, long long& sy,
-                                         long long& sz, int& o, int n, bool valid, bool noisy,
-                                         unsigned long long quad, unsigned noise_id,
-                                         unsigned key0, unsigned key1) {
-  float tap[4][8];
-  int lab[4];
-  const long long s0x = sx, s0y = sy, s0z = sz;
-#pragma unroll
-  for (int m = 0; m < 4; ++m) {
-    lab[m] = P.fill_label;
-#pragma unroll
-    for (int d = 0; d < 8; ++d) tap[m][d] = P.fill;
-    if (MODE != MODE_EXTERIOR && m < n) {
-      const int fx = q40_floor(sx), fy = q40_floor(sy), fz = q40_floor(sz);
-      const int hbx = q40_halfbit(sx), hby = q40_halfbit(sy), hbz = q40_halfbit(sz);
-      if (MODE == MODE_INTERIOR) {
-        const int base = (fz * P.ny + fy) * P.nx + fx;
-        if (IMG) {
-          const TIn* p = P.img + base;
-          tap[m][0] = ld_val(p);
-          tap[m][1] = ld_val(p + 1);
-          tap[m][2] = ld_val(p + P.nx);
-          tap[m][3] = ld_val(p + P.nx + 1);
-          tap[m][4] = ld_val(p + P.nxy);
-          tap[m][5] = ld_val(p + P.nxy + 1);
-          tap[m][6] = ld_val(p + P.nxy + P.nx);
-          tap[m][7] = ld_val(p + P.nxy + P.nx + 1);
-        }
-        if (LAB) lab[m] = __ldg(P.lab + (base + hbx + hby * P.nx + hbz * P.nxy));
-      } else {
-        if (IMG) {
-          const bool x0 = (unsigned)fx < (unsigned)P.nx, x1 = (unsigned)(fx + 1) < (unsigned)P.nx;
-          const bool y0 = (unsigned)fy < (unsigned)P.ny, y1 = (unsigned)(fy + 1) < (unsigned)P.ny;
-          const bool z0 = (unsigned)fz < (unsigned)P.nz, z1 = (unsigned)(fz + 1) < (unsigned)P.nz;
-          // Unsigned arithmetic wraps harmlessly far outside; an index is only
-          // dereferenced when its tap lies inside the volume.
-          const unsigned ux = (unsigned)P.nx, uxy = (unsigned)P.nxy;
-          const unsigned b = ((unsigned)fz * (unsigned)P.ny + (unsigned)fy) * ux + (unsigned)fx;
-          if (x0 && y0 && z0) tap[m][0] = ld_val(P.img + b);
-          if (x1 && y0 && z0) tap[m][1] = ld_val(P.img + (b + 1u));
-          if (x0 && y1 && z0) tap[m][2] = ld_val(P.img + (b + ux));
-          if (x1 && y1 && z0) tap[m][3] = ld_val(P.img + (b + ux + 1u));
-          if (x0 && y0 && z1) tap[m][4] = ld_val(P.img + (b + uxy));
-          if (x1 && y0 && z1) tap[m][5] = ld_val(P.img + (b + uxy + 1u));
-          if (x0 && y1 && z1) tap[m][6] = ld_val(P.img + (b + uxy + ux));
-          if (x1 && y1 && z1) tap[m][7] = ld_val(P.img + (b + uxy + ux + 1u));
-        }
-        if (LAB) {
-          const int rx = fx + hbx, ry = fy + hby, rz = fz + hbz;
-          if ((unsigned)rx < (unsigned)P.nx && (unsigned)ry < (unsigned)P.ny &&
-              (unsigned)rz < (unsigned)P.nz)
-            lab[m] = __ldg(P.lab + ((rz * P.ny + ry) * P.nx + rx));
-        }
-      }
-    }
-    sx += P.dx;
-    sy += P.dy;
-    sz += P.dz;
-  }
-  float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-  if (noisy) quad_normals(quad, noise_id, key0, key1, z);
-  long long cx = s0x, cy = s0y, cz = s0z;
+// Exterior quad: every tap reads the fill value, so the sample is constant;
+// only the noise differs per voxel.  The coordinate advances by n steps at once.
+template <typename TIn, bool IMG, bool LAB>
+__device__ __forceinline__ void fwd_quad_exterior(const FwdP<TIn>& P, int& o, int n, bool valid,
+                                                  const float z[4]) {
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
     if (m < n) {
-      if (IMG) {
-        float v = P.fill;
-        if (MODE != MODE_EXTERIOR) {
-          const float tx = q40_frac(cx), ty = q40_frac(cy), tz = q40_frac(cz);
-          const float c00 = fmaf(tx, tap[m][1] - tap[m][0], tap[m][0]);
-          const float c10 = fmaf(tx, tap[m][3] - tap[m][2], tap[m][2]);
-          const float c01 = fmaf(tx, tap[m][5] - tap[m][4], tap[m][4]);
-          const float c11 = fmaf(tx, tap[m][7] - tap[m][6], tap[m][6]);
-          const float c0 = fmaf(ty, c10 - c00, c00);
-          const float c1 = fmaf(ty, c11 - c01, c01);
-          v = fmaf(tz, c1 - c0, c0);
-        }
-        if (valid) __stcs(P.oimg + o, fmaf(P.sigma, z[m], fmaf(P.a, v, P.b)));
+      if (valid) {
+        if (IMG) __stcs(P.oimg + o, fmaf(P.sigma, z[m], P.yfill));
+        if (LAB) P.olab[o] = (uint8_t)P.fill_label;
       }
-      if (LAB && valid) P.olab[o] = (uint8_t)lab[m];
-      cx += P.dx;
-      cy += P.dy;
-      cz += P.dz;
       o += P.plane;
     }
   }
 }
 
-template <typename TIn, int NW, int QZ, bool IMG, bool LAB>
+// Interior / general quad (n = 1..4 z-consecutive voxels, warp-uniform MODE),
+// software-pipelined in groups of PD voxels: the coordinates are stepped
+// once, every tap and label load of a group is issued before any of its
+// samples is interpolated, and the quad's normals are computed while the
+// first group's loads are in flight.  PD trades registers (occupancy) for
+// memory-level parallelism; it is part of the kernel variant.
+template <typename TIn, int MODE, bool IMG, bool LAB, bool FULL, int PD>
+__device__ __forceinline__ void fwd_quad(const FwdP<TIn>& P, long long& sx, long long& sy,
+                                         long long& sz, int& o, int n, bool valid,
+                                         bool noisy, unsigned long long quad, unsigned noise_id,
+                                         unsigned key0, unsigned key1) {
+  float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+  for (int g0 = 0; g0 < 4; g0 += PD) {
+    float tap[PD][8];
+    float w[PD][3];
+    int lab[PD];
+#pragma unroll
+    for (int i = 0; i < PD; ++i) {
+      const int m = g0 + i;
+      lab[i] = P.fill_label;
+#pragma unroll
+      for (int d = 0; d < 8; ++d) tap[i][d] = P.fill;
+      w[i][0] = w[i][1] = w[i][2] = 0.0f;
+      if (FULL || m < n) {
+        const int fx = q40_floor(sx), fy = q40_floor(sy), fz = q40_floor(sz);
+        const int hbx = q40_halfbit(sx), hby = q40_halfbit(sy), hbz = q40_halfbit(sz);
+        if (IMG) {
+          w[i][0] = q40_frac(sx);
+          w[i][1] = q40_frac(sy);
+          w[i][2] = q40_frac(sz);
+        }
+        if (MODE == MODE_INTERIOR) {
+          const int base = (fz * P.ny + fy) * P.nx + fx;
+          if (IMG) {
+            const TIn* p = P.img + base;
+            tap[i][0] = ld_val(p);
+            tap[i][1] = ld_val(p + 1);
+            tap[i][2] = ld_val(p + P.nx);
+            tap[i][3] = ld_val(p + P.nx + 1);
+            tap[i][4] = ld_val(p + P.nxy);
+            tap[i][5] = ld_val(p + P.nxy + 1);
+            tap[i][6] = ld_val(p + P.nxy + P.nx);
+            tap[i][7] = ld_val(p + P.nxy + P.nx + 1);
+          }
+          if (LAB) lab[i] = __ldg(P.lab + (base + hbx + hby * P.nx + hbz * P.nxy));
+        } else {
+          if (IMG) {
+            const bool x0 = (unsigned)fx < (unsigned)P.nx,
+                       x1 = (unsigned)(fx + 1) < (unsigned)P.nx;
+            const bool y0 = (unsigned)fy < (unsigned)P.ny,
+                       y1 = (unsigned)(fy + 1) < (unsigned)P.ny;
+            const bool z0 = (unsigned)fz < (unsigned)P.nz,
+                       z1 = (unsigned)(fz + 1) < (unsigned)P.nz;
+            // Unsigned arithmetic wraps harmlessly far outside; an index is only
+            // dereferenced when its tap lies inside the volume.
+            const unsigned ux = (unsigned)P.nx, uxy = (unsigned)P.nxy;
+            const unsigned b =
+                ((unsigned)fz * (unsigned)P.ny + (unsigned)fy) * ux + (unsigned)fx;
+            if (x0 && y0 && z0) tap[i][0] = ld_val(P.img + b);
+            if (x1 && y0 && z0) tap[i][1] = ld_val(P.img + (b + 1u));
+            if (x0 && y1 && z0) tap[i][2] = ld_val(P.img + (b + ux));
+            if (x1 && y1 && z0) tap[i][3] = ld_val(P.img + (b + ux + 1u));
+            if (x0 && y0 && z1) tap[i][4] = ld_val(P.img + (b + uxy));
+            if (x1 && y0 && z1) tap[i][5] = ld_val(P.img + (b + uxy + 1u));
+            if (x0 && y1 && z1) tap[i][6] = ld_val(P.img + (b + uxy + ux));
+            if (x1 && y1 && z1) tap[i][7] = ld_val(P.img + (b + uxy + ux + 1u));
+          }
+          if (LAB) {
+            const int rx = fx + hbx, ry = fy + hby, rz = fz + hbz;
+            if ((unsigned)rx < (unsigned)P.nx && (unsigned)ry < (unsigned)P.ny &&
+                (unsigned)rz < (unsigned)P.nz)
+              lab[i] = __ldg(P.lab + ((rz * P.ny + ry) * P.nx + rx));
+          }
+        }
+        sx += P.dx;
+        sy += P.dy;
+        sz += P.dz;
+      }
+    }
+    if (g0 == 0 && noisy) quad_normals(quad, noise_id, key0, key1, z);
+#pragma unroll
+    for (int i = 0; i < PD; ++i) {
+      const int m = g0 + i;
+      if (FULL || m < n) {
+        if (IMG) {
+          const float tx = w[i][0], ty = w[i][1], tz = w[i][2];
+          const float c00 = fmaf(tx, tap[i][1] - tap[i][0], tap[i][0]);
+          const float c10 = fmaf(tx, tap[i][3] - tap[i][2], tap[i][2]);
+          const float c01 = fmaf(tx, tap[i][5] - tap[i][4], tap[i][4]);
+          const float c11 = fmaf(tx, tap[i][7] - tap[i][6], tap[i][6]);
+          const float c0 = fmaf(ty, c10 - c00, c00);
+          const float c1 = fmaf(ty, c11 - c01, c01);
+          const float v = fmaf(tz, c1 - c0, c0);
+          if (valid) __stcs(P.oimg + o, fmaf(P.sigma, z[m], fmaf(P.a, v, P.b)));
+        }
+        if (LAB && valid) P.olab[o] = (uint8_t)lab[i];
+        o += P.plane;
+      }
+    }
+  }
+}
+
+template <typename TIn, int NW, int QZ, int PD, bool IMG, bool LAB>
 __device__ __forceinline__ void fwd_tile_t(const VolConst& vc, int t, unsigned key0,
                                            unsigned key1) {
   const TileCoord tc = tile_coord<NW, QZ>(t, vc.onx, vc.ony, vc.onz);
@@ -146,6 +173,7 @@ __device__ __forceinline__ void fwd_tile_t(const VolConst& vc, int t, unsigned k
   P.b = vc.b;
   P.sigma = vc.sigma;
   P.fill = vc.fill;
+  P.yfill = fmaf(vc.a, vc.fill, vc.b);
   const unsigned noise_id = vc.noise_id;
   const bool noisy = IMG && vc.sigma > 0.0f;
   const unsigned onx = (unsigned)vc.onx, ony = (unsigned)vc.ony;
@@ -163,42 +191,51 @@ __device__ __forceinline__ void fwd_tile_t(const VolConst& vc, int t, unsigned k
         ((unsigned long long)(kq >> 2) * ony + (unsigned)tc.jc) * onx + (unsigned)tc.ic;
     const long long s[3] = {sx, sy, sz};
     const int mode = warp_mode(classify_run<true>(s, ds, n - 1, P.nx, P.ny, P.nz));
-    if (mode == MODE_INTERIOR)
-      fwd_quad<TIn, MODE_INTERIOR, IMG, LAB>(P, sx, sy, sz, o, n, tc.valid, noisy, quad,
-                                             noise_id, key0, key1);
-    else if (mode == MODE_EXTERIOR)
-      fwd_quad<TIn, MODE_EXTERIOR, IMG, LAB>(P, sx, sy, sz, o, n, tc.valid, noisy, quad,
-                                             noise_id, key0, key1);
-    else
-      fwd_quad<TIn, MODE_GENERAL, IMG, LAB>(P, sx, sy, sz, o, n, tc.valid, noisy, quad,
-                                            noise_id, key0, key1);
+    if (mode == MODE_EXTERIOR) {
+      float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      if (noisy) quad_normals(quad, noise_id, key0, key1, z);
+      fwd_quad_exterior<TIn, IMG, LAB>(P, o, n, tc.valid, z);
+      sx += (long long)n * P.dx;
+      sy += (long long)n * P.dy;
+      sz += (long long)n * P.dz;
+    } else if (n == 4) {
+      if (mode == MODE_INTERIOR)
+        fwd_quad<TIn, MODE_INTERIOR, IMG, LAB, true, PD>(P, sx, sy, sz, o, 4, tc.valid, noisy, quad,
+                                                     noise_id, key0, key1);
+      else
+        fwd_quad<TIn, MODE_GENERAL, IMG, LAB, true, PD>(P, sx, sy, sz, o, 4, tc.valid, noisy, quad,
+                                                    noise_id, key0, key1);
+    } else {
+      fwd_quad<TIn, MODE_GENERAL, IMG, LAB, false, PD>(P, sx, sy, sz, o, n, tc.valid, noisy, quad,
+                                                   noise_id, key0, key1);
+    }
   }
 }
 
-template <int NW, int QZ>
+template <int NW, int QZ, int PD>
 __device__ __forceinline__ void fwd_tile(const VolConst& vc, int t, unsigned key0,
                                          unsigned key1) {
   const bool img = vc.out_image != nullptr, lab = vc.out_label != nullptr;
   if (vc.dtype == AUG_I16) {
     if (img && lab)
-      fwd_tile_t<int16_t, NW, QZ, true, true>(vc, t, key0, key1);
+      fwd_tile_t<int16_t, NW, QZ, PD, true, true>(vc, t, key0, key1);
     else if (img)
-      fwd_tile_t<int16_t, NW, QZ, true, false>(vc, t, key0, key1);
+      fwd_tile_t<int16_t, NW, QZ, PD, true, false>(vc, t, key0, key1);
     else
-      fwd_tile_t<int16_t, NW, QZ, false, true>(vc, t, key0, key1);
+      fwd_tile_t<int16_t, NW, QZ, PD, false, true>(vc, t, key0, key1);
   } else {
     if (img && lab)
-      fwd_tile_t<float, NW, QZ, true, true>(vc, t, key0, key1);
+      fwd_tile_t<float, NW, QZ, PD, true, true>(vc, t, key0, key1);
     else if (img)
-      fwd_tile_t<float, NW, QZ, true, false>(vc, t, key0, key1);
+      fwd_tile_t<float, NW, QZ, PD, true, false>(vc, t, key0, key1);
     else
-      fwd_tile_t<float, NW, QZ, false, true>(vc, t, key0, key1);
+      fwd_tile_t<float, NW, QZ, PD, false, true>(vc, t, key0, key1);
   }
 }
 
 // MB: minimum resident CTAs per SM requested from the register allocator
 // (1 = no constraint); part of the variant, chosen by measurement.
-template <int NW, int QZ, int MB>
+template <int NW, int QZ, int MB, int PD>
 __global__ void __launch_bounds__(NW * 32, MB)
     k_fwd_batched(const aug_volume_desc* __restrict__ descs, int n_vols,
                   const VolConst* __restrict__ tab, unsigned key0, unsigned key1) {
@@ -208,18 +245,18 @@ __global__ void __launch_bounds__(NW * 32, MB)
       [&](int v, int t, long long) {
         const VolConst& vc = tab[v];
         if (vc.ok && (vc.out_image != nullptr || vc.out_label != nullptr))
-          fwd_tile<NW, QZ>(vc, t, key0, key1);
+          fwd_tile<NW, QZ, PD>(vc, t, key0, key1);
       });
 }
 
-template <int NW, int QZ, int MB>
+template <int NW, int QZ, int MB, int PD>
 __global__ void __launch_bounds__(NW * 32, MB)
     k_fwd_volume(const aug_volume_desc desc, unsigned key0, unsigned key1) {
   __shared__ VolConst vc;
   if (threadIdx.x == 0) make_volconst(desc, desc_valid(desc, desc.out_image != nullptr, false), vc);
   __syncthreads();
   if (!vc.ok) return;
-  fwd_tile<NW, QZ>(vc, blockIdx.x, key0, key1);
+  fwd_tile<NW, QZ, PD>(vc, blockIdx.x, key0, key1);
 }
 
 // ---- host launchers ----------------------------------------------------------
@@ -231,16 +268,18 @@ struct FwdVariant {
   FwdBK batched;
   FwdVK volume;
 };
-#define FWD_V(NW, QZ, MB) \
-  { NW, QZ, k_fwd_batched<NW, QZ, MB>, k_fwd_volume<NW, QZ, MB> }
-const FwdVariant kFwd[] = {FWD_V(4, 8, 1), FWD_V(4, 8, 6),  FWD_V(8, 4, 1), FWD_V(8, 4, 3),
-                           FWD_V(4, 4, 6), FWD_V(8, 8, 3),  FWD_V(8, 2, 3), FWD_V(16, 2, 1),
-                           FWD_V(4, 8, 8), FWD_V(8, 4, 4)};
+#define FWD_V(NW, QZ, MB, PD) \
+  { NW, QZ, k_fwd_batched<NW, QZ, MB, PD>, k_fwd_volume<NW, QZ, MB, PD> }
+// (warps per CTA, quads per thread, min CTAs per SM, pipeline depth)
+const FwdVariant kFwd[] = {FWD_V(4, 8, 1, 2),  FWD_V(4, 8, 6, 2), FWD_V(4, 8, 8, 2),
+                           FWD_V(8, 4, 3, 2),  FWD_V(8, 4, 4, 2), FWD_V(4, 8, 1, 4),
+                           FWD_V(4, 8, 6, 4),  FWD_V(8, 4, 3, 4), FWD_V(8, 2, 4, 2),
+                           FWD_V(16, 2, 2, 2), FWD_V(4, 4, 8, 2)};
 #undef FWD_V
-const char* kFwdNames[] = {"tile32x4x32",     "tile32x4x32_24w", "tile32x8x16",
-                           "tile32x8x16_24w", "tile32x4x16_24w", "tile32x8x32_24w",
-                           "tile32x8x8_24w",  "tile32x16x8",     "tile32x4x32_32w",
-                           "tile32x8x16_32w"};
+const char* kFwdNames[] = {"t32x4x32_pd2",     "t32x4x32_pd2_24w", "t32x4x32_pd2_32w",
+                           "t32x8x16_pd2_24w", "t32x8x16_pd2_32w", "t32x4x32_pd4",
+                           "t32x4x32_pd4_24w", "t32x8x16_pd4_24w", "t32x8x8_pd2_32w",
+                           "t32x16x8_pd2_32w", "t32x4x16_pd2_32w"};
 }  // namespace
 
 int fwd_num_variants() { return (int)(sizeof(kFwd) / sizeof(kFwd[0])); }
