@@ -182,6 +182,34 @@ __device__ __forceinline__ void fwd_tile_t(const VolConst& vc, int t, unsigned k
   long long sz = coord_q40(vc.tq[2], tc.ic, tc.jc, tc.k0);
   const long long ds[3] = {P.dx, P.dy, P.dz};
   int o = (tc.k0 * vc.ony + tc.jc) * vc.onx + tc.ic;
+  // One warp vote for the whole z-run; quads are re-classified only when the
+  // run straddles the input boundary.
+  const long long s0[3] = {sx, sy, sz};
+  const int run_mode = warp_mode(classify_run<true>(s0, ds, tc.k1 - 1 - tc.k0, P.nx, P.ny, P.nz));
+  const bool full_run = tc.k1 - tc.k0 == 4 * QZ;
+  if (run_mode == MODE_EXTERIOR) {
+#pragma unroll 1
+    for (int kq = tc.k0; kq < tc.k1; kq += 4) {
+      const int n = min(4, tc.k1 - kq);
+      float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      if (noisy)
+        quad_normals(((unsigned long long)(kq >> 2) * ony + (unsigned)tc.jc) * onx +
+                         (unsigned)tc.ic,
+                     noise_id, key0, key1, z);
+      fwd_quad_exterior<TIn, IMG, LAB>(P, o, n, tc.valid, z);
+    }
+    return;
+  }
+  if (run_mode == MODE_INTERIOR && full_run) {
+#pragma unroll 1
+    for (int kq = tc.k0; kq < tc.k1; kq += 4) {
+      const unsigned long long quad =
+          ((unsigned long long)(kq >> 2) * ony + (unsigned)tc.jc) * onx + (unsigned)tc.ic;
+      fwd_quad<TIn, MODE_INTERIOR, IMG, LAB, true, PD>(P, sx, sy, sz, o, 4, tc.valid, noisy, quad,
+                                                       noise_id, key0, key1);
+    }
+    return;
+  }
 #pragma unroll 1
   for (int q = 0; q < QZ; ++q) {
     const int kq = tc.k0 + 4 * q;
