@@ -299,15 +299,15 @@ struct FwdVariant {
 #define FWD_V(NW, QZ, MB, PD) \
   { NW, QZ, k_fwd_batched<NW, QZ, MB, PD>, k_fwd_volume<NW, QZ, MB, PD> }
 // (warps per CTA, quads per thread, min CTAs per SM, pipeline depth)
-const FwdVariant kFwd[] = {FWD_V(4, 8, 1, 2),  FWD_V(4, 8, 6, 2), FWD_V(4, 8, 8, 2),
-                           FWD_V(8, 4, 3, 2),  FWD_V(8, 4, 4, 2), FWD_V(4, 8, 1, 4),
-                           FWD_V(4, 8, 6, 4),  FWD_V(8, 4, 3, 4), FWD_V(8, 2, 4, 2),
-                           FWD_V(16, 2, 2, 2), FWD_V(4, 4, 8, 2)};
+const FwdVariant kFwd[] = {FWD_V(4, 8, 8, 2),  FWD_V(4, 8, 1, 2),  FWD_V(4, 8, 6, 4),
+                           FWD_V(4, 8, 8, 1),  FWD_V(4, 8, 12, 1), FWD_V(4, 8, 10, 2),
+                           FWD_V(8, 4, 4, 1),  FWD_V(8, 4, 6, 1),  FWD_V(8, 4, 4, 2),
+                           FWD_V(4, 4, 12, 1), FWD_V(2, 8, 16, 1)};
 #undef FWD_V
-const char* kFwdNames[] = {"t32x4x32_pd2",     "t32x4x32_pd2_24w", "t32x4x32_pd2_32w",
-                           "t32x8x16_pd2_24w", "t32x8x16_pd2_32w", "t32x4x32_pd4",
-                           "t32x4x32_pd4_24w", "t32x8x16_pd4_24w", "t32x8x8_pd2_32w",
-                           "t32x16x8_pd2_32w", "t32x4x16_pd2_32w"};
+const char* kFwdNames[] = {"t32x4x32_pd2_32w", "t32x4x32_pd2",     "t32x4x32_pd4_24w",
+                           "t32x4x32_pd1_32w", "t32x4x32_pd1_48w", "t32x4x32_pd2_40w",
+                           "t32x8x16_pd1_32w", "t32x8x16_pd1_48w", "t32x8x16_pd2_32w",
+                           "t32x4x16_pd1_48w", "t32x2x32_pd1_32w"};
 }  // namespace
 
 int fwd_num_variants() { return (int)(sizeof(kFwd) / sizeof(kFwd[0])); }
