@@ -179,6 +179,34 @@ aug_status iou_loss_fwd_bwd(const aug_volume_desc* d_descs, int n_vols, const fl
                             int n_classes, float* d_loss, float* d_grad_p, void* d_workspace,
                             size_t workspace_bytes, aug_stream_t stream);
 
+/* ---- allocation-free variant of iou_loss_fwd_bwd --------------------------------
+ * The paper has no counterpart to this entry point; it exists for callers
+ * that must not allocate device memory: plug-ins hosted by a framework that
+ * owns the whole device memory budget and hands out no scratch buffers, and
+ * latency-critical loops that may not allocate once they have started (an
+ * allocation can block on the device and take milliseconds).
+ *
+ * Computes exactly what iou_loss_fwd_bwd computes (same arguments and
+ * layouts), but instead of a caller-provided workspace it uses one
+ * fixed-size scratch array (about 3.2 MB) that the library keeps in device
+ * memory on every GPU that loads it, until the process exits.  The caller
+ * still passes all inputs and outputs.  No device memory is allocated by this
+ * call or by the library on its behalf.
+ *
+ * Limits: 1 <= n_vols <= 64 (else AUG_ERR_INVALID_ARG), 1 <= n_classes <= 8
+ * (else AUG_ERR_UNSUPPORTED); at most 256 thread blocks per pass.
+ * d_status: NULL, or a device int32[2] that receives (status, bad volume) of
+ * this call's descriptor checks (0, 0 when every descriptor is valid).
+ *
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  All calls share the one array and each call overwrites it, so
+ * calls that may overlap on the GPU (different streams, or several host
+ * threads) race and give wrong results: serialise them. */
+aug_status iou_loss_fwd_bwd_noalloc(const aug_volume_desc* d_descs, int n_vols,
+                                    const float* d_p, int n_classes, float* d_loss,
+                                    float* d_grad_p, int* d_status, aug_stream_t stream);
+
 /* ---- kernel variants and autotuning -----------------------------------------
  * op: 0 = aug_warp_fwd, 1 = aug_warp_bwd, 2 = iou_loss_fwd_bwd.
  * Variants differ in tile shape (warps per CTA along y, z-run per thread);

@@ -64,6 +64,8 @@ def _load():
     L.aug_warp_bwd.restype = i32
     L.iou_loss_fwd_bwd.argtypes = [vp, i32, vp, i32, vp, vp, vp, sz, vp]
     L.iou_loss_fwd_bwd.restype = i32
+    L.iou_loss_fwd_bwd_noalloc.argtypes = [vp, i32, vp, i32, vp, vp, vp, vp]
+    L.iou_loss_fwd_bwd_noalloc.restype = i32
     L.aug_num_variants.argtypes = [i32]
     L.aug_num_variants.restype = i32
     L.aug_variant_name.argtypes = [i32, i32]
@@ -160,6 +162,17 @@ def iou_loss_fwd_bwd(d_descs: torch.Tensor, n_vols: int, p: torch.Tensor, n_clas
     _check(_L.iou_loss_fwd_bwd(_ptr(d_descs), int(n_vols), _ptr(p), int(n_classes),
                                _ptr(loss), _ptr(grad_p), _ptr(workspace), workspace.numel(),
                                _stream(stream)), "iou_loss_fwd_bwd")
+
+
+def iou_loss_fwd_bwd_noalloc(d_descs: torch.Tensor, n_vols: int, p: torch.Tensor,
+                             n_classes: int, loss: torch.Tensor, grad_p: Optional[torch.Tensor],
+                             status: Optional[torch.Tensor] = None, stream=None):
+    """iou_loss_fwd_bwd without a caller workspace: the library's own fixed
+    scratch array is used (at most 64 volumes, 8 classes).  ``status``: optional
+    int32[2] CUDA tensor receiving (device status, bad volume)."""
+    _check(_L.iou_loss_fwd_bwd_noalloc(_ptr(d_descs), int(n_vols), _ptr(p), int(n_classes),
+                                       _ptr(loss), _ptr(grad_p), _ptr(status), _stream(stream)),
+           "iou_loss_fwd_bwd_noalloc")
 
 
 def aug_philox4x32_10(ctr: torch.Tensor, seed: int, stream=None) -> torch.Tensor:
