@@ -21,11 +21,19 @@
 
 namespace augk {
 
-template <typename TIn, int MODE, bool GIN, bool GT>
+// Scatter target of the input gradient: the caller's grad_in volume
+// (global atomics), or a shared-memory brick covering the tile's input
+// bounding box (shared atomics; index = x + y*bsy + z*bsz + boff).
+struct BrickMap {
+  float* brick;
+  int bsy, bsz, boff;
+};
+
+template <typename TIn, int MODE, bool GIN, bool GT, bool SMEM>
 __device__ __forceinline__ void bwd_run(const VolConst& vc, const TileCoord& tc, long long sx,
                                         long long sy, long long sz,
                                         const float* __restrict__ g, float* __restrict__ gin,
-                                        float acc[6]) {
+                                        const BrickMap& bm, float acc[6]) {
   const TIn* __restrict__ img = (const TIn*)vc.image;
   const long long dx = vc.tq[0][2], dy = vc.tq[1][2], dz = vc.tq[2][2];
   const int nx = vc.nx, ny = vc.ny, nz = vc.nz, nxy = nx * ny;
@@ -42,31 +50,37 @@ __device__ __forceinline__ void bwd_run(const VolConst& vc, const TileCoord& tc,
       const float wz1 = t.tz, wz0 = 1.0f - t.tz;
       const float g00 = ga * wy0 * wz0, g10 = ga * wy1 * wz0;
       const float g01 = ga * wy0 * wz1, g11 = ga * wy1 * wz1;
+      const int sy_ = SMEM ? bm.bsy : nx, sz_ = SMEM ? bm.bsz : nxy;
       if (MODE == MODE_INTERIOR) {
-        float* p = gin + ((t.fz * ny + t.fy) * nx + t.fx);
+        float* p = SMEM ? bm.brick + (t.fx + t.fy * bm.bsy + t.fz * bm.bsz + bm.boff)
+                        : gin + ((t.fz * ny + t.fy) * nx + t.fx);
         atomicAdd(p, g00 * wx0);
         atomicAdd(p + 1, g00 * wx1);
-        atomicAdd(p + nx, g10 * wx0);
-        atomicAdd(p + nx + 1, g10 * wx1);
-        atomicAdd(p + nxy, g01 * wx0);
-        atomicAdd(p + nxy + 1, g01 * wx1);
-        atomicAdd(p + nxy + nx, g11 * wx0);
-        atomicAdd(p + nxy + nx + 1, g11 * wx1);
+        atomicAdd(p + sy_, g10 * wx0);
+        atomicAdd(p + sy_ + 1, g10 * wx1);
+        atomicAdd(p + sz_, g01 * wx0);
+        atomicAdd(p + sz_ + 1, g01 * wx1);
+        atomicAdd(p + sz_ + sy_, g11 * wx0);
+        atomicAdd(p + sz_ + sy_ + 1, g11 * wx1);
       } else {
         const bool x0 = (unsigned)t.fx < (unsigned)nx, x1 = (unsigned)(t.fx + 1) < (unsigned)nx;
         const bool y0 = (unsigned)t.fy < (unsigned)ny, y1 = (unsigned)(t.fy + 1) < (unsigned)ny;
         const bool z0 = (unsigned)t.fz < (unsigned)nz, z1 = (unsigned)(t.fz + 1) < (unsigned)nz;
-        const unsigned base = ((unsigned)t.fz * (unsigned)ny + (unsigned)t.fy) * (unsigned)nx +
-                              (unsigned)t.fx;
-        const unsigned ux = (unsigned)nx, uxy = (unsigned)nxy;
-        if (x0 && y0 && z0) atomicAdd(gin + base, g00 * wx0);
-        if (x1 && y0 && z0) atomicAdd(gin + (base + 1u), g00 * wx1);
-        if (x0 && y1 && z0) atomicAdd(gin + (base + ux), g10 * wx0);
-        if (x1 && y1 && z0) atomicAdd(gin + (base + ux + 1u), g10 * wx1);
-        if (x0 && y0 && z1) atomicAdd(gin + (base + uxy), g01 * wx0);
-        if (x1 && y0 && z1) atomicAdd(gin + (base + uxy + 1u), g01 * wx1);
-        if (x0 && y1 && z1) atomicAdd(gin + (base + uxy + ux), g11 * wx0);
-        if (x1 && y1 && z1) atomicAdd(gin + (base + uxy + ux + 1u), g11 * wx1);
+        // Indices are formed in unsigned arithmetic (wrapping harmlessly far
+        // outside) and only used for taps inside the volume.
+        const unsigned base = SMEM ? (unsigned)(t.fx + t.fy * bm.bsy + t.fz * bm.bsz + bm.boff)
+                                   : ((unsigned)t.fz * (unsigned)ny + (unsigned)t.fy) *
+                                             (unsigned)nx + (unsigned)t.fx;
+        float* p0 = SMEM ? bm.brick : gin;
+        const unsigned ux = (unsigned)sy_, uxy = (unsigned)sz_;
+        if (x0 && y0 && z0) atomicAdd(p0 + base, g00 * wx0);
+        if (x1 && y0 && z0) atomicAdd(p0 + (base + 1u), g00 * wx1);
+        if (x0 && y1 && z0) atomicAdd(p0 + (base + ux), g10 * wx0);
+        if (x1 && y1 && z0) atomicAdd(p0 + (base + ux + 1u), g10 * wx1);
+        if (x0 && y0 && z1) atomicAdd(p0 + (base + uxy), g01 * wx0);
+        if (x1 && y0 && z1) atomicAdd(p0 + (base + uxy + 1u), g01 * wx1);
+        if (x0 && y1 && z1) atomicAdd(p0 + (base + uxy + ux), g11 * wx0);
+        if (x1 && y1 && z1) atomicAdd(p0 + (base + uxy + ux + 1u), g11 * wx1);
       }
     }
     if (GT) {
@@ -98,9 +112,10 @@ struct BwdShared {
   double acc[12];
 };
 
-template <typename TIn, int NW, int QZ, bool GIN, bool GT>
+template <typename TIn, int NW, int QZ, bool GIN, bool GT, bool SMEM = false>
 __device__ __forceinline__ void bwd_tile(const VolConst& vc, BwdShared<NW>& sh, int t,
-                                         const float* g, float* gin) {
+                                         const float* g, float* gin,
+                                         const BrickMap& bm = BrickMap{nullptr, 0, 0, 0}) {
   const TileCoord tc = tile_coord<NW, QZ>(t, vc.onx, vc.ony, vc.onz);
   long long s[3], ds[3];
 #pragma unroll
@@ -113,9 +128,9 @@ __device__ __forceinline__ void bwd_tile(const VolConst& vc, BwdShared<NW>& sh, 
       warp_mode(classify_run<true>(s, ds, tc.k1 - 1 - tc.k0, vc.nx, vc.ny, vc.nz));
   // Exterior cells have all taps equal to the fill value: no gradient at all.
   if (mode == MODE_INTERIOR)
-    bwd_run<TIn, MODE_INTERIOR, GIN, GT>(vc, tc, s[0], s[1], s[2], g, gin, acc);
+    bwd_run<TIn, MODE_INTERIOR, GIN, GT, SMEM>(vc, tc, s[0], s[1], s[2], g, gin, bm, acc);
   else if (mode == MODE_GENERAL)
-    bwd_run<TIn, MODE_GENERAL, GIN, GT>(vc, tc, s[0], s[1], s[2], g, gin, acc);
+    bwd_run<TIn, MODE_GENERAL, GIN, GT, SMEM>(vc, tc, s[0], s[1], s[2], g, gin, bm, acc);
   if (GT) {
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const float fi = (float)tc.ic, fj = (float)tc.jc;
@@ -185,6 +200,111 @@ __global__ void __launch_bounds__(NW * 32)
   flush();
 }
 
+// Input bounding box of one output tile: the tile is a box of output indices,
+// its image under the affine map is a parallelepiped whose coordinate extrema
+// sit at the 8 corners, so floor(min)..floor(max)+1 per axis (clipped to the
+// volume) holds every in-volume tap of the tile.  Threads 0..2 each reduce one
+// axis; lo > hi means no in-volume tap on that axis.
+template <int NW, int QZ>
+__device__ __forceinline__ void tile_bbox(const VolConst& vc, int t, int* lo, int* hi) {
+  if (threadIdx.x < 3) {
+    const int r = threadIdx.x;
+    const int tx_n = (vc.onx + 31) / 32, ty_n = (vc.ony + NW - 1) / NW;
+    const int tx = t % tx_n, ty = (t / tx_n) % ty_n, tz = t / (tx_n * ty_n);
+    const int i0 = tx * 32, j0 = ty * NW, k0 = tz * 4 * QZ;
+    const int ii[2] = {i0, min(i0 + 31, vc.onx - 1)};
+    const int jj[2] = {j0, min(j0 + NW - 1, vc.ony - 1)};
+    const int kk[2] = {k0, min(k0 + 4 * QZ - 1, vc.onz - 1)};
+    int mn = 0x7fffffff, mx = -0x7fffffff;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int f = q40_floor(coord_q40(vc.tq[r], ii[c & 1], jj[(c >> 1) & 1], kk[c >> 2]));
+      mn = min(mn, f);
+      mx = max(mx, f);
+    }
+    const int n = r == 0 ? vc.nx : (r == 1 ? vc.ny : vc.nz);
+    lo[r] = max(mn, 0);
+    hi[r] = min(mx + 1, n - 1);
+  }
+}
+
+// Adjoint with the input gradient accumulated per tile in a shared-memory
+// brick (CAP floats) and flushed with coalesced global atomics, one per
+// non-zero brick element, row by row.  Tiles whose bounding box exceeds the
+// brick fall back to direct global atomics.  The flush leaves the brick
+// zeroed for the next tile.
+template <int NW, int QZ, bool GT, int CAP>
+__global__ void __launch_bounds__(NW * 32)
+    k_bwd_smem(const aug_volume_desc* __restrict__ descs, int n_vols,
+               const VolConst* __restrict__ tab, const float* const* gout, float* const* gin,
+               double* partials) {
+  extern __shared__ float brick[];
+  __shared__ BwdShared<NW> sh;
+  __shared__ SchedSmem<NW * 32> sm;
+  __shared__ int box_lo[3], box_hi[3];
+  for (int e = threadIdx.x; e < CAP; e += blockDim.x) brick[e] = 0.0f;
+  int staged = -1;
+  auto flush_partials = [&]() {
+    if (GT && staged >= 0 && threadIdx.x < 12)
+      partials[((size_t)blockIdx.x * n_vols + staged) * 12 + threadIdx.x] = sh.acc[threadIdx.x];
+  };
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for_each_tile<NW, QZ>(
+      descs, n_vols, sm,
+      [&](int c0, int cnt) {
+        if (GT)
+          for (int i = threadIdx.x; i < cnt * 12; i += blockDim.x)
+            partials[((size_t)blockIdx.x * n_vols + c0) * 12 + i] = 0.0;
+        __syncthreads();
+      },
+      [&](int v, int t, long long) {
+        if (v != staged) {
+          flush_partials();
+          if (GT && threadIdx.x < 12) sh.acc[threadIdx.x] = 0.0;
+          staged = v;
+        }
+        const VolConst& vc = tab[v];
+        if (!vc.ok) return;
+        const float* g = gout[v];
+        float* gi = gin[v];
+        __syncthreads();  // every thread is done with the previous tile's box
+        tile_bbox<NW, QZ>(vc, t, box_lo, box_hi);
+        __syncthreads();
+        const int lx = box_lo[0], ly = box_lo[1], lz = box_lo[2];
+        const int bx = box_hi[0] - lx + 1, by = box_hi[1] - ly + 1, bz = box_hi[2] - lz + 1;
+        const bool empty = bx <= 0 || by <= 0 || bz <= 0;
+        const long long size = empty ? 0 : (long long)bx * by * bz;
+        if (size > 0 && size <= CAP) {
+          const BrickMap bm{brick, bx, bx * by, -(lx + ly * bx + lz * bx * by)};
+          if (vc.dtype == AUG_I16)
+            bwd_tile<int16_t, NW, QZ, true, GT, true>(vc, sh, t, g, gi, bm);
+          else
+            bwd_tile<float, NW, QZ, true, GT, true>(vc, sh, t, g, gi, bm);
+          __syncthreads();
+          const int nxy = vc.nx * vc.ny;
+          for (int row = warp; row < by * bz; row += NW) {
+            const int ey = row % by, ez = row / by;
+            float* src = brick + row * bx;
+            float* dst = gi + ((lz + ez) * nxy + (ly + ey) * vc.nx + lx);
+            for (int ex = lane; ex < bx; ex += 32) {
+              const float val = src[ex];
+              if (val != 0.0f) {
+                atomicAdd(dst + ex, val);
+                src[ex] = 0.0f;
+              }
+            }
+          }
+          __syncthreads();
+        } else {
+          if (vc.dtype == AUG_I16)
+            bwd_tile<int16_t, NW, QZ, true, GT, false>(vc, sh, t, g, gi);
+          else
+            bwd_tile<float, NW, QZ, true, GT, false>(vc, sh, t, g, gi);
+        }
+      });
+  flush_partials();
+}
+
 // Zero every grad_in volume (float32 input shape) before the scatter.
 __global__ void k_zero_grad_in(const aug_volume_desc* __restrict__ descs, int n_vols,
                                float* const* gin) {
@@ -228,19 +348,29 @@ namespace {
 using BwdK = void (*)(const aug_volume_desc*, int, const VolConst*, const float* const*,
                       float* const*, double*);
 struct BwdVariant {
-  int nw, qz;
-  BwdK k[4];  // [GIN*2 + GT]
+  int nw, qz, cap;  // cap > 0: input gradient through a shared brick of cap floats
+  BwdK k[4];        // [GIN*2 + GT]
 };
 #define BWD_V(NW, QZ)                                                                  \
   {                                                                                    \
-    NW, QZ,                                                                            \
+    NW, QZ, 0,                                                                         \
         {k_bwd_batched<NW, QZ, false, false>, k_bwd_batched<NW, QZ, false, true>,      \
          k_bwd_batched<NW, QZ, true, false>, k_bwd_batched<NW, QZ, true, true> }       \
   }
-const BwdVariant kBwd[] = {BWD_V(8, 4), BWD_V(4, 4), BWD_V(8, 2), BWD_V(8, 8), BWD_V(4, 8)};
+#define BWD_S(NW, QZ, CAP)                                                             \
+  {                                                                                    \
+    NW, QZ, CAP,                                                                       \
+        {k_bwd_batched<NW, QZ, false, false>, k_bwd_batched<NW, QZ, false, true>,      \
+         k_bwd_smem<NW, QZ, false, CAP>, k_bwd_smem<NW, QZ, true, CAP> }               \
+  }
+const BwdVariant kBwd[] = {BWD_S(8, 4, 24576), BWD_S(8, 2, 16384), BWD_S(4, 4, 16384),
+                           BWD_S(8, 4, 32768), BWD_S(16, 2, 24576), BWD_V(8, 4),
+                           BWD_V(4, 4),        BWD_V(8, 2),        BWD_V(8, 8)};
 #undef BWD_V
-const char* kBwdNames[] = {"tile32x8x16", "tile32x4x16", "tile32x8x8", "tile32x8x32",
-                           "tile32x4x32"};
+#undef BWD_S
+const char* kBwdNames[] = {"t32x8x16_brick96k", "t32x8x8_brick64k", "t32x4x16_brick64k",
+                           "t32x8x16_brick128k", "t32x16x8_brick96k", "t32x8x16_atomic",
+                           "t32x4x16_atomic",    "t32x8x8_atomic",    "t32x8x32_atomic"};
 }  // namespace
 
 int bwd_num_variants() { return (int)(sizeof(kBwd) / sizeof(kBwd[0])); }
@@ -263,9 +393,15 @@ cudaError_t launch_bwd(int variant, const aug_volume_desc* d, int n, const float
   }
   const BwdK kern = bv.k[(want_gin ? 2 : 0) + (want_gt ? 1 : 0)];
   const int block = bv.nw * 32;
-  const int grid = persistent_grid((const void*)kern, block, 0);
+  const size_t smem = (want_gin && bv.cap > 0) ? (size_t)bv.cap * sizeof(float) : 0;
+  if (smem > 48 * 1024) {
+    e = cudaFuncSetAttribute((const void*)kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  const int grid = persistent_grid((const void*)kern, block, smem);
   if (grid <= 0) return cudaErrorInvalidConfiguration;
-  kern<<<grid, block, 0, st>>>(d, n, tab, gout, gin, partials);
+  kern<<<grid, block, smem, st>>>(d, n, tab, gout, gin, partials);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (want_gt) {
     k_bwd_finalize<<<n, 384, 0, st>>>(partials, grid, n, gaff);
