@@ -363,14 +363,14 @@ struct BwdVariant {
         {k_bwd_batched<NW, QZ, false, false>, k_bwd_batched<NW, QZ, false, true>,      \
          k_bwd_smem<NW, QZ, false, CAP>, k_bwd_smem<NW, QZ, true, CAP> }               \
   }
-const BwdVariant kBwd[] = {BWD_S(8, 4, 24576), BWD_S(8, 2, 16384), BWD_S(4, 4, 16384),
-                           BWD_S(8, 4, 32768), BWD_S(16, 2, 24576), BWD_V(8, 4),
-                           BWD_V(4, 4),        BWD_V(8, 2),        BWD_V(8, 8)};
+const BwdVariant kBwd[] = {BWD_V(8, 4),         BWD_V(4, 4),        BWD_V(8, 2),
+                           BWD_V(8, 8),         BWD_S(16, 2, 24576), BWD_S(8, 2, 16384),
+                           BWD_S(8, 4, 24576)};
 #undef BWD_V
 #undef BWD_S
-const char* kBwdNames[] = {"t32x8x16_brick96k", "t32x8x8_brick64k", "t32x4x16_brick64k",
-                           "t32x8x16_brick128k", "t32x16x8_brick96k", "t32x8x16_atomic",
-                           "t32x4x16_atomic",    "t32x8x8_atomic",    "t32x8x32_atomic"};
+const char* kBwdNames[] = {"t32x8x16_atomic",   "t32x4x16_atomic",  "t32x8x8_atomic",
+                           "t32x8x32_atomic",   "t32x16x8_brick96k", "t32x8x8_brick64k",
+                           "t32x8x16_brick96k"};
 }  // namespace
 
 int bwd_num_variants() { return (int)(sizeof(kBwd) / sizeof(kBwd[0])); }
