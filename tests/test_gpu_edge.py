@@ -45,9 +45,9 @@ def test_adjoint_many_volumes_across_scheduler_chunks():
     grads = upstream_grads([v.out_shape for v in cases], seed=3, device="cuda")
     gin, gaff = run_bwd(cases, grads)
     for b, v in enumerate(cases):
-        ri, rt, dv = ref.warp_bwd(v, grads[b], want_dvds=True)
+        ri, rt, _ = ref.warp_bwd(v, grads[b])
         G.check_grad(gin[b], ri, f"grad_in {b}")
-        floor = 1e-7 * G.summand_scale(v, grads[b].cpu().numpy(), dv)
+        floor = 1e-7 * G.summand_scale(v, grads[b].cpu().numpy())
         G.check_grad_affine(gaff[b], rt, f"grad_T {b}", floor=floor)
 
 
