@@ -128,6 +128,37 @@ __device__ __forceinline__ float ld_val<int16_t>(const int16_t* p) {
   return (float)__ldg(p);
 }
 
+// ---- packed FP32 pairs (sm_100+ f32x2 instructions) ----------------------------
+// Two independent float lanes in one 64-bit register; each lane is rounded
+// exactly like the scalar instruction, so packed and scalar code give
+// bitwise-identical results.
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 pk2(float lo, float hi) {
+  f32x2 r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+  return r;
+}
+__device__ __forceinline__ void upk2(f32x2 r, float& lo, float& hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(r));
+}
+__device__ __forceinline__ f32x2 fma2(f32x2 a, f32x2 b, f32x2 c) {
+  f32x2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+__device__ __forceinline__ f32x2 sub2(f32x2 a, f32x2 b) {
+  f32x2 d;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+// Fractions of two Q.40 coordinates, packed (see q40_frac).
+__device__ __forceinline__ f32x2 q40_frac2(long long s0, long long s1) {
+  const unsigned m0 = (unsigned)((unsigned long long)s0 >> 17) & 0x7FFFFFu;
+  const unsigned m1 = (unsigned)((unsigned long long)s1 >> 17) & 0x7FFFFFu;
+  return sub2(pk2(__uint_as_float(0x3F800000u | m0), __uint_as_float(0x3F800000u | m1)),
+              pk2(1.0f, 1.0f));
+}
+
 // ---- Philox4x32-10 (Salmon et al., SC'11) -----------------------------------
 // Round: (hi0, lo0) = M0 * c0, (hi1, lo1) = M1 * c2;
 //        c <- (hi1 ^ c1 ^ k0, lo1, hi0 ^ c3 ^ k1, lo0); key += Weyl constants.

@@ -129,6 +129,37 @@ __device__ __forceinline__ void fwd_quad(const FwdP<TIn>& P, long long& sx, long
       }
     }
     if (g0 == 0 && noisy) quad_normals(quad, noise_id, key0, key1, z);
+    if (FULL && IMG && PD >= 2) {
+      // Voxel pairs share packed f32x2 instructions (same rounding as scalar).
+#pragma unroll
+      for (int i = 0; i < PD; i += 2) {
+        const int m = g0 + i;
+        const f32x2 tx = pk2(w[i][0], w[i + 1][0]), ty = pk2(w[i][1], w[i + 1][1]);
+        const f32x2 tz = pk2(w[i][2], w[i + 1][2]);
+        f32x2 v0[8];
+#pragma unroll
+        for (int d = 0; d < 8; ++d) v0[d] = pk2(tap[i][d], tap[i + 1][d]);
+        const f32x2 c00 = fma2(tx, sub2(v0[1], v0[0]), v0[0]);
+        const f32x2 c10 = fma2(tx, sub2(v0[3], v0[2]), v0[2]);
+        const f32x2 c01 = fma2(tx, sub2(v0[5], v0[4]), v0[4]);
+        const f32x2 c11 = fma2(tx, sub2(v0[7], v0[6]), v0[6]);
+        const f32x2 c0 = fma2(ty, sub2(c10, c00), c00);
+        const f32x2 c1 = fma2(ty, sub2(c11, c01), c01);
+        const f32x2 v = fma2(tz, sub2(c1, c0), c0);
+        const f32x2 y = fma2(pk2(P.sigma, P.sigma), pk2(z[m], z[m + 1]),
+                             fma2(pk2(P.a, P.a), v, pk2(P.b, P.b)));
+        float y0, y1;
+        upk2(y, y0, y1);
+        if (valid) {
+          __stcs(P.oimg + o, y0);
+          if (LAB) P.olab[o] = (uint8_t)lab[i];
+          __stcs(P.oimg + o + P.plane, y1);
+          if (LAB) P.olab[o + P.plane] = (uint8_t)lab[i + 1];
+        }
+        o += 2 * P.plane;
+      }
+      continue;
+    }
 #pragma unroll
     for (int i = 0; i < PD; ++i) {
       const int m = g0 + i;
