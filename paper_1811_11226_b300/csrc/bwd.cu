@@ -46,6 +46,7 @@ __device__ __forceinline__ void bwd_run(const VolConst& vc, const TileCoord& tc,
     Taps t;
     load_taps<TIn, MODE>(img, sx, sy, sz, nx, ny, nz, fill, t);
     if (GIN && tc.valid) {
+#define RADD(p, v) (SMEM ? red_add_shared((p), (v)) : red_add_global((p), (v)))
       const float wx1 = t.tx, wx0 = 1.0f - t.tx, wy1 = t.ty, wy0 = 1.0f - t.ty;
       const float wz1 = t.tz, wz0 = 1.0f - t.tz;
       const float g00 = ga * wy0 * wz0, g10 = ga * wy1 * wz0;
@@ -54,14 +55,14 @@ __device__ __forceinline__ void bwd_run(const VolConst& vc, const TileCoord& tc,
       if (MODE == MODE_INTERIOR) {
         float* p = SMEM ? bm.brick + (t.fx + t.fy * bm.bsy + t.fz * bm.bsz + bm.boff)
                         : gin + ((t.fz * ny + t.fy) * nx + t.fx);
-        atomicAdd(p, g00 * wx0);
-        atomicAdd(p + 1, g00 * wx1);
-        atomicAdd(p + sy_, g10 * wx0);
-        atomicAdd(p + sy_ + 1, g10 * wx1);
-        atomicAdd(p + sz_, g01 * wx0);
-        atomicAdd(p + sz_ + 1, g01 * wx1);
-        atomicAdd(p + sz_ + sy_, g11 * wx0);
-        atomicAdd(p + sz_ + sy_ + 1, g11 * wx1);
+        RADD(p, g00 * wx0);
+        RADD(p + 1, g00 * wx1);
+        RADD(p + sy_, g10 * wx0);
+        RADD(p + sy_ + 1, g10 * wx1);
+        RADD(p + sz_, g01 * wx0);
+        RADD(p + sz_ + 1, g01 * wx1);
+        RADD(p + sz_ + sy_, g11 * wx0);
+        RADD(p + sz_ + sy_ + 1, g11 * wx1);
       } else {
         const bool x0 = (unsigned)t.fx < (unsigned)nx, x1 = (unsigned)(t.fx + 1) < (unsigned)nx;
         const bool y0 = (unsigned)t.fy < (unsigned)ny, y1 = (unsigned)(t.fy + 1) < (unsigned)ny;
@@ -73,16 +74,17 @@ __device__ __forceinline__ void bwd_run(const VolConst& vc, const TileCoord& tc,
                                              (unsigned)nx + (unsigned)t.fx;
         float* p0 = SMEM ? bm.brick : gin;
         const unsigned ux = (unsigned)sy_, uxy = (unsigned)sz_;
-        if (x0 && y0 && z0) atomicAdd(p0 + base, g00 * wx0);
-        if (x1 && y0 && z0) atomicAdd(p0 + (base + 1u), g00 * wx1);
-        if (x0 && y1 && z0) atomicAdd(p0 + (base + ux), g10 * wx0);
-        if (x1 && y1 && z0) atomicAdd(p0 + (base + ux + 1u), g10 * wx1);
-        if (x0 && y0 && z1) atomicAdd(p0 + (base + uxy), g01 * wx0);
-        if (x1 && y0 && z1) atomicAdd(p0 + (base + uxy + 1u), g01 * wx1);
-        if (x0 && y1 && z1) atomicAdd(p0 + (base + uxy + ux), g11 * wx0);
-        if (x1 && y1 && z1) atomicAdd(p0 + (base + uxy + ux + 1u), g11 * wx1);
+        if (x0 && y0 && z0) RADD(p0 + base, g00 * wx0);
+        if (x1 && y0 && z0) RADD(p0 + (base + 1u), g00 * wx1);
+        if (x0 && y1 && z0) RADD(p0 + (base + ux), g10 * wx0);
+        if (x1 && y1 && z0) RADD(p0 + (base + ux + 1u), g10 * wx1);
+        if (x0 && y0 && z1) RADD(p0 + (base + uxy), g01 * wx0);
+        if (x1 && y0 && z1) RADD(p0 + (base + uxy + 1u), g01 * wx1);
+        if (x0 && y1 && z1) RADD(p0 + (base + uxy + ux), g11 * wx0);
+        if (x1 && y1 && z1) RADD(p0 + (base + uxy + ux + 1u), g11 * wx1);
       }
     }
+#undef RADD
     if (GT) {
       float c00, c10, c01, c11, c0, c1;
       trilerp(t, c00, c10, c01, c11, c0, c1);
@@ -289,7 +291,7 @@ __global__ void __launch_bounds__(NW * 32)
             for (int ex = lane; ex < bx; ex += 32) {
               const float val = src[ex];
               if (val != 0.0f) {
-                atomicAdd(dst + ex, val);
+                red_add_global(dst + ex, val);
                 src[ex] = 0.0f;
               }
             }

@@ -128,6 +128,19 @@ __device__ __forceinline__ float ld_val<int16_t>(const int16_t* p) {
   return (float)__ldg(p);
 }
 
+// ---- fire-and-forget reductions -------------------------------------------------
+// atomicAdd with an unused result may still be emitted as a returning atomic,
+// whose destination register the warp then waits for; the reduction forms
+// below never return a value.
+__device__ __forceinline__ void red_add_global(float* p, float v) {
+  asm volatile("red.global.add.f32 [%0], %1;" ::"l"(p), "f"(v) : "memory");
+}
+__device__ __forceinline__ void red_add_shared(float* p, float v) {
+  asm volatile("red.shared.add.f32 [%0], %1;" ::"r"((unsigned)__cvta_generic_to_shared(p)),
+               "f"(v)
+               : "memory");
+}
+
 // ---- packed FP32 pairs (sm_100+ f32x2 instructions) ----------------------------
 // Two independent float lanes in one 64-bit register; each lane is rounded
 // exactly like the scalar instruction, so packed and scalar code give
