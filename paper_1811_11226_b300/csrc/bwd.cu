@@ -40,29 +40,51 @@ __device__ __forceinline__ void bwd_run(const VolConst& vc, const TileCoord& tc,
   const int plane = vc.onx * vc.ony;
   const float a = vc.a, fill = vc.fill;
   int o = (tc.k0 * vc.ony + tc.jc) * vc.onx + tc.ic;
+  // Interior runs merge along z: when the next voxel's cell is the current
+  // one moved by +1 in z, the four z+1 contributions of this voxel land on the
+  // next voxel's four z taps; they are held in registers and added there
+  // instead of being issued as separate reductions.
+  float pend[4] = {0.f, 0.f, 0.f, 0.f};
+  int pend_base = -1;
+  const int sy_ = SMEM ? bm.bsy : nx, sz_ = SMEM ? bm.bsz : nxy;
+  float* const tgt = SMEM ? bm.brick : gin;
+#define RADD(p, v) (SMEM ? red_add_shared((p), (v)) : red_add_global((p), (v)))
 #pragma unroll 4
   for (int k = tc.k0; k < tc.k1; ++k) {
     const float ga = tc.valid ? a * __ldcs(g + o) : 0.0f;
     Taps t;
     load_taps<TIn, MODE>(img, sx, sy, sz, nx, ny, nz, fill, t);
     if (GIN && tc.valid) {
-#define RADD(p, v) (SMEM ? red_add_shared((p), (v)) : red_add_global((p), (v)))
       const float wx1 = t.tx, wx0 = 1.0f - t.tx, wy1 = t.ty, wy0 = 1.0f - t.ty;
       const float wz1 = t.tz, wz0 = 1.0f - t.tz;
       const float g00 = ga * wy0 * wz0, g10 = ga * wy1 * wz0;
       const float g01 = ga * wy0 * wz1, g11 = ga * wy1 * wz1;
-      const int sy_ = SMEM ? bm.bsy : nx, sz_ = SMEM ? bm.bsz : nxy;
       if (MODE == MODE_INTERIOR) {
-        float* p = SMEM ? bm.brick + (t.fx + t.fy * bm.bsy + t.fz * bm.bsz + bm.boff)
-                        : gin + ((t.fz * ny + t.fy) * nx + t.fx);
-        RADD(p, g00 * wx0);
-        RADD(p + 1, g00 * wx1);
-        RADD(p + sy_, g10 * wx0);
-        RADD(p + sy_ + 1, g10 * wx1);
-        RADD(p + sz_, g01 * wx0);
-        RADD(p + sz_ + 1, g01 * wx1);
-        RADD(p + sz_ + sy_, g11 * wx0);
-        RADD(p + sz_ + sy_ + 1, g11 * wx1);
+        const int base = SMEM ? t.fx + t.fy * bm.bsy + t.fz * bm.bsz + bm.boff
+                              : (t.fz * ny + t.fy) * nx + t.fx;
+        float c0 = g00 * wx0, c1 = g00 * wx1, c2 = g10 * wx0, c3 = g10 * wx1;
+        if (base == pend_base) {
+          c0 += pend[0];
+          c1 += pend[1];
+          c2 += pend[2];
+          c3 += pend[3];
+        } else if (pend_base >= 0) {
+          float* q = tgt + pend_base;
+          RADD(q, pend[0]);
+          RADD(q + 1, pend[1]);
+          RADD(q + sy_, pend[2]);
+          RADD(q + sy_ + 1, pend[3]);
+        }
+        float* p = tgt + base;
+        RADD(p, c0);
+        RADD(p + 1, c1);
+        RADD(p + sy_, c2);
+        RADD(p + sy_ + 1, c3);
+        pend[0] = g01 * wx0;
+        pend[1] = g01 * wx1;
+        pend[2] = g11 * wx0;
+        pend[3] = g11 * wx1;
+        pend_base = base + sz_;
       } else {
         const bool x0 = (unsigned)t.fx < (unsigned)nx, x1 = (unsigned)(t.fx + 1) < (unsigned)nx;
         const bool y0 = (unsigned)t.fy < (unsigned)ny, y1 = (unsigned)(t.fy + 1) < (unsigned)ny;
@@ -72,19 +94,17 @@ __device__ __forceinline__ void bwd_run(const VolConst& vc, const TileCoord& tc,
         const unsigned base = SMEM ? (unsigned)(t.fx + t.fy * bm.bsy + t.fz * bm.bsz + bm.boff)
                                    : ((unsigned)t.fz * (unsigned)ny + (unsigned)t.fy) *
                                              (unsigned)nx + (unsigned)t.fx;
-        float* p0 = SMEM ? bm.brick : gin;
         const unsigned ux = (unsigned)sy_, uxy = (unsigned)sz_;
-        if (x0 && y0 && z0) RADD(p0 + base, g00 * wx0);
-        if (x1 && y0 && z0) RADD(p0 + (base + 1u), g00 * wx1);
-        if (x0 && y1 && z0) RADD(p0 + (base + ux), g10 * wx0);
-        if (x1 && y1 && z0) RADD(p0 + (base + ux + 1u), g10 * wx1);
-        if (x0 && y0 && z1) RADD(p0 + (base + uxy), g01 * wx0);
-        if (x1 && y0 && z1) RADD(p0 + (base + uxy + 1u), g01 * wx1);
-        if (x0 && y1 && z1) RADD(p0 + (base + uxy + ux), g11 * wx0);
-        if (x1 && y1 && z1) RADD(p0 + (base + uxy + ux + 1u), g11 * wx1);
+        if (x0 && y0 && z0) RADD(tgt + base, g00 * wx0);
+        if (x1 && y0 && z0) RADD(tgt + (base + 1u), g00 * wx1);
+        if (x0 && y1 && z0) RADD(tgt + (base + ux), g10 * wx0);
+        if (x1 && y1 && z0) RADD(tgt + (base + ux + 1u), g10 * wx1);
+        if (x0 && y0 && z1) RADD(tgt + (base + uxy), g01 * wx0);
+        if (x1 && y0 && z1) RADD(tgt + (base + uxy + 1u), g01 * wx1);
+        if (x0 && y1 && z1) RADD(tgt + (base + uxy + ux), g11 * wx0);
+        if (x1 && y1 && z1) RADD(tgt + (base + uxy + ux + 1u), g11 * wx1);
       }
     }
-#undef RADD
     if (GT) {
       float c00, c10, c01, c11, c0, c1;
       trilerp(t, c00, c10, c01, c11, c0, c1);
@@ -106,6 +126,14 @@ __device__ __forceinline__ void bwd_run(const VolConst& vc, const TileCoord& tc,
     sz += dz;
     o += plane;
   }
+  if (GIN && MODE == MODE_INTERIOR && pend_base >= 0) {
+    float* q = tgt + pend_base;
+    RADD(q, pend[0]);
+    RADD(q + 1, pend[1]);
+    RADD(q + sy_, pend[2]);
+    RADD(q + sy_ + 1, pend[3]);
+  }
+#undef RADD
 }
 
 template <int NW>
