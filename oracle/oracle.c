@@ -17,6 +17,12 @@
  *   label        nearest voxel, floor(s + 1/2), fill label outside
  *                                                     (Sec. 4, nearest neighbour)
  *   intensity    y = a v + beta + sigma n,  n ~ N(0, 1) (Sec. 4, additive noise)
+ *   occlusion    optional: output voxels with z0 <= k <= z0 + dz (output z index)
+ *                are 0 and skip every later step (Sec. 4, random occlusion)
+ *   window       optional: y <- min(max(y, 0), 1) after the noise; with
+ *                a = 1/(hi - lo), beta = -lo/(hi - lo) and sigma scaled by a
+ *                this is the window/level map clamp((I - lo)/(hi - lo), 0, 1)
+ *                applied to the noisy image (Sec. 4, window/level)
  *   noise        Philox4x32-10 (Salmon et al., SC'11) + Box-Muller
  *   adjoint      d(out)/d(input) and d(out)/d(T) of the above
  *   IOU loss     1 - |py|_1 / (|p|_1 + |y|_1 - |py|_1), per class
@@ -125,12 +131,21 @@ typedef struct {
   int fill_label;
   uint64_t seed;
   uint32_t noise_id;
+  int flags;  /* 1: clamp to [0, 1] (window/level), 2: occlusion */
+  double occ_z0, occ_dz;
 } volume;
+
+#define ORACLE_CLAMP01 1
+#define ORACLE_OCCLUDE 2
 
 static void load_volume(volume* v, const void* image, int image_is_i16, const uint8_t* label,
                         int64_t nx, int64_t ny, int64_t nz, int64_t onx, int64_t ony,
                         int64_t onz, const float* T12, float a, float beta, float sigma,
-                        float fill, int fill_label, uint64_t seed, uint32_t noise_id) {
+                        float fill, int fill_label, uint64_t seed, uint32_t noise_id, int flags,
+                        float occ_z0, float occ_dz) {
+  v->flags = flags;
+  v->occ_z0 = occ_z0;
+  v->occ_dz = occ_dz;
   v->image = image;
   v->image_is_i16 = image_is_i16;
   v->label = label;
@@ -200,15 +215,25 @@ static int near_tie(const double s[3]) {
   return 0;
 }
 
+static int occluded(const volume* v, int64_t k) {
+  return (v->flags & ORACLE_OCCLUDE) && (double)k >= v->occ_z0 &&
+         (double)k <= v->occ_z0 + v->occ_dz;
+}
+
 static void one_voxel(const volume* v, int64_t i, int64_t j, int64_t k, double* out_val,
                       uint8_t* out_lab, uint8_t* tie) {
   double s[3];
   coordinate(v, i, j, k, s);
   if (out_val) {
-    double val = v->a * trilinear(v, s) + v->beta;
-    if (v->sigma != 0.0)
-      val += v->sigma * noise_normal(v->seed, v->noise_id, v->onx, v->ony, i, j, k);
-    *out_val = val;
+    if (occluded(v, k)) {
+      *out_val = 0.0;
+    } else {
+      double val = v->a * trilinear(v, s) + v->beta;
+      if (v->sigma != 0.0)
+        val += v->sigma * noise_normal(v->seed, v->noise_id, v->onx, v->ony, i, j, k);
+      if (v->flags & ORACLE_CLAMP01) val = val < 0.0 ? 0.0 : (val > 1.0 ? 1.0 : val);
+      *out_val = val;
+    }
   }
   if (out_lab) *out_lab = (uint8_t)nearest_label(v, s);
   if (tie) *tie = (uint8_t)near_tie(s);
@@ -222,11 +247,11 @@ ORACLE_EXPORT int64_t oracle_warp_fwd(const void* image, int image_is_i16,
                                       int64_t nz, int64_t onx, int64_t ony, int64_t onz,
                                       const float* T12, float a, float beta, float sigma,
                                       float fill, int fill_label, uint64_t seed,
-                                      uint32_t noise_id, double* out_image,
-                                      uint8_t* out_label, uint8_t* tie) {
+                                      uint32_t noise_id, int flags, float occ_z0, float occ_dz,
+                                      double* out_image, uint8_t* out_label, uint8_t* tie) {
   volume v;
   load_volume(&v, image, image_is_i16, label, nx, ny, nz, onx, ony, onz, T12, a, beta, sigma,
-              fill, fill_label, seed, noise_id);
+              fill, fill_label, seed, noise_id, flags, occ_z0, occ_dz);
   int64_t ties = 0;
   size_t q = 0;
   for (int64_t k = 0; k < onz; ++k)
@@ -247,12 +272,13 @@ ORACLE_EXPORT void oracle_warp_fwd_points(const void* image, int image_is_i16,
                                           int64_t nz, int64_t onx, int64_t ony, int64_t onz,
                                           const float* T12, float a, float beta, float sigma,
                                           float fill, int fill_label, uint64_t seed,
-                                          uint32_t noise_id, const int64_t* q, int64_t n,
+                                          uint32_t noise_id, int flags, float occ_z0,
+                                          float occ_dz, const int64_t* q, int64_t n,
                                           double* out_image, uint8_t* out_label,
                                           uint8_t* tie) {
   volume v;
   load_volume(&v, image, image_is_i16, label, nx, ny, nz, onx, ony, onz, T12, a, beta, sigma,
-              fill, fill_label, seed, noise_id);
+              fill, fill_label, seed, noise_id, flags, occ_z0, occ_dz);
   for (int64_t m = 0; m < n; ++m) {
     int64_t i = q[m] % onx, j = (q[m] / onx) % ony, k = q[m] / (onx * ony);
     one_voxel(&v, i, j, k, out_image ? out_image + m : NULL,
@@ -268,18 +294,20 @@ ORACLE_EXPORT void oracle_warp_fwd_points(const void* image, int image_is_i16,
 /*   dv/ds_r     = sum_d (d_r ? +1 : -1) prod_{q != r} (d_q ? t_q : 1 - t_q)  */
 /*                 V(f + d)     (right derivative where s_r is an integer)   */
 /*   grad_T[r][c] = sum_o a g(o) dv/ds_r(o) obar_c(o), obar = (i, j, k, 1).  */
-/* Fill taps contribute to dv/ds but not to grad_in.                         */
+/* Fill taps contribute to dv/ds but not to grad_in.  Occluded output voxels  */
+/* (flags & 2) contribute nothing.  The clamp of flags & 1 is not modelled:    */
+/* the adjoint is defined for unclamped outputs.                              */
 /* grad_in (input shape, overwritten), grad_T (12) and dvds (3 per output     */
 /* voxel) may each be NULL.                                                  */
 /* ------------------------------------------------------------------------ */
 ORACLE_EXPORT void oracle_warp_bwd(const void* image, int image_is_i16, int64_t nx,
                                    int64_t ny, int64_t nz, int64_t onx, int64_t ony,
-                                   int64_t onz, const float* T12, float a, float fill,
-                                   const float* g, double* grad_in, double* grad_T,
-                                   double* dvds) {
+                                   int64_t onz, const float* T12, float a, float fill, int flags,
+                                   float occ_z0, float occ_dz, const float* g, double* grad_in,
+                                   double* grad_T, double* dvds) {
   volume v;
   load_volume(&v, image, image_is_i16, NULL, nx, ny, nz, onx, ony, onz, T12, a, 0.0f, 0.0f,
-              fill, 0, 0, 0);
+              fill, 0, 0, 0, flags, occ_z0, occ_dz);
   if (grad_in) memset(grad_in, 0, sizeof(double) * (size_t)(nx * ny * nz));
   double gt[3][4] = {{0}};
   size_t q = 0;
@@ -292,7 +320,8 @@ ORACLE_EXPORT void oracle_warp_bwd(const void* image, int image_is_i16, int64_t 
           f[r] = floor(s[r]);
           t[r] = s[r] - f[r];
         }
-        double ga = v.a * (double)g[q];
+        /* An occluded voxel is the constant 0: no gradient flows through it. */
+        double ga = occluded(&v, k) ? 0.0 : v.a * (double)g[q];
         double dv[3] = {0.0, 0.0, 0.0};
         for (int d = 0; d < 8; ++d) {
           int dd[3] = {d & 1, (d >> 1) & 1, (d >> 2) & 1};

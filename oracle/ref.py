@@ -32,12 +32,12 @@ def lib():
             L.oracle_philox_many.argtypes = [_u64, _vp, _i64, _vp]
             L.oracle_noise.argtypes = [_u64, _u32, _i64, _i64, _vp, _i64, _vp]
             fwd_args = [_vp, _int, _vp, _i64, _i64, _i64, _i64, _i64, _i64, _vp, _f32, _f32,
-                        _f32, _f32, _int, _u64, _u32]
+                        _f32, _f32, _int, _u64, _u32, _int, _f32, _f32]
             L.oracle_warp_fwd.argtypes = fwd_args + [_vp, _vp, _vp]
             L.oracle_warp_fwd.restype = _i64
             L.oracle_warp_fwd_points.argtypes = fwd_args + [_vp, _i64, _vp, _vp, _vp]
             L.oracle_warp_bwd.argtypes = [_vp, _int, _i64, _i64, _i64, _i64, _i64, _i64, _vp,
-                                          _f32, _f32, _vp, _vp, _vp, _vp]
+                                          _f32, _f32, _int, _f32, _f32, _vp, _vp, _vp, _vp]
             L.oracle_iou.argtypes = [_vp, _vp, _int, _i64, C.c_double, _vp, _vp, _vp]
             _lib = L
     return _lib
@@ -74,6 +74,12 @@ def noise(seed: int, noise_id: int, onx: int, ony: int, q):
     return z
 
 
+def _extra(v):
+    """Optional window/level and occlusion fields (flags, occ_z0, occ_dz)."""
+    return [int(getattr(v, "flags", 0)), _f32(getattr(v, "occ_z0", 0.0)),
+            _f32(getattr(v, "occ_dz", 0.0))]
+
+
 def _vol_args(v, seed):
     img = _np(v.image)
     if img.dtype not in (np.float32, np.int16):
@@ -85,7 +91,7 @@ def _vol_args(v, seed):
     keep = (img, lab, T)
     args = [_ptr(img), int(img.dtype == np.int16), _ptr(lab), nx, ny, nz, onx, ony, onz,
             _ptr(T), _f32(v.photo_a), _f32(v.photo_b), _f32(v.sigma), _f32(v.fill_image),
-            int(v.fill_label), _u64(seed), _u32(v.noise_id)]
+            int(v.fill_label), _u64(seed), _u32(v.noise_id), *_extra(v)]
     return args, keep
 
 
@@ -131,8 +137,8 @@ def warp_bwd(v, g, want_grad_in=True, want_dvds=False):
     gt = np.empty(12, np.float64)
     dv = np.empty((onz, ony, onx, 3), np.float64) if want_dvds else None
     lib().oracle_warp_bwd(_ptr(img), int(img.dtype == np.int16), nx, ny, nz, onx, ony, onz,
-                          _ptr(T), _f32(v.photo_a), _f32(v.fill_image), _ptr(g), _ptr(gi),
-                          _ptr(gt), _ptr(dv))
+                          _ptr(T), _f32(v.photo_a), _f32(v.fill_image), *_extra(v), _ptr(g),
+                          _ptr(gi), _ptr(gt), _ptr(dv))
     return gi, gt.reshape(3, 4), dv
 
 

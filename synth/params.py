@@ -69,3 +69,26 @@ def random_photometric(rng: np.random.Generator, a_range=(0.9, 1.1),
     b = np.float32(rng.uniform(*b_range))
     sigma = np.float32(rng.uniform(*sigma_range))
     return a, b, sigma
+
+
+def random_window_occlusion(rng: np.random.Generator, onz: int, lo_range=(-1000.0, -150.0),
+                            hi_range=(230.0, 1500.0), sigma_range=(0.0, 50.0),
+                            max_occ_frac=0.3):
+    """Window/level and occlusion parameters of Sec. 4, as descriptor fields.
+
+    Window [lo, hi] drawn from the given HU ranges; noise sigma in HU.  The
+    window map clamp((I + n - lo)/(hi - lo), 0, 1) equals the intensity affine
+    a = 1/(hi - lo), b = -lo/(hi - lo) with noise sigma * a, then a clamp.
+    Occlusion: a z-slab of the output of height d ~ U[0, d_max] starting at
+    z ~ U[-d_max, onz - 1], d_max = max_occ_frac * onz, so every slice is
+    equally likely to be covered.  Returns (a, b, sigma, occ_z0, occ_dz), float32.
+    """
+    lo = rng.uniform(*lo_range)
+    hi = rng.uniform(*hi_range)
+    a = 1.0 / (hi - lo)
+    b = -lo / (hi - lo)
+    sigma = rng.uniform(*sigma_range) * a
+    dmax = max_occ_frac * onz
+    dz = rng.uniform(0.0, dmax)
+    z0 = rng.uniform(-dmax, onz - 1)
+    return (np.float32(a), np.float32(b), np.float32(sigma), np.float32(z0), np.float32(dz))

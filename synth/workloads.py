@@ -45,6 +45,9 @@ class VolumeCase:
     fill_image: np.float32 = np.float32(FILL_HU)
     fill_label: int = 0
     noise_id: int = 0
+    flags: int = 0            # 1: window/level clamp to [0, 1]; 2: occlusion
+    occ_z0: np.float32 = np.float32(0.0)
+    occ_dz: np.float32 = np.float32(0.0)
 
     @property
     def in_shape(self):
