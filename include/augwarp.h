@@ -28,7 +28,8 @@
  *   - Output value: y = photo_a * v + photo_b + noise_sigma * n, with n a
  *     standard normal from Philox4x32-10 (key = seed, counter = (quad index,
  *     noise_id)) and Box-Muller; quads are four z-consecutive output voxels
- *     (k = 4m..4m+3) -- see aug_warp_fwd.
+ *     (k = 4m..4m+3) -- see aug_warp_fwd.  Optional per volume (aug_flags):
+ *     occlusion of a z-slab of the output and a window/level clamp.
  *   - All pointers are DEVICE pointers unless stated otherwise.  The caller
  *     owns every buffer; the library allocates no device memory in any entry
  *     point.  Every entry point only enqueues work on `stream` and returns
@@ -69,6 +70,18 @@ typedef enum {
 
 typedef enum { AUG_F32 = 0, AUG_I16 = 1 } aug_dtype;
 
+/* Descriptor flags (Sec. 4, the photometric steps after the warp). */
+typedef enum {
+  /* Window/level: clamp the output to [0, 1] after the noise.  With
+   * photo_a = 1/(hi - lo), photo_b = -lo/(hi - lo) and noise_sigma scaled by
+   * photo_a this is clamp((I + n - lo)/(hi - lo), 0, 1). */
+  AUG_FLAG_WINDOW = 1,
+  /* Random occlusion: output voxels whose z index k satisfies
+   * occ_z0 <= k <= occ_z0 + occ_dz are 0, and nothing else is computed for
+   * them (no fetch, no noise, no window).  Labels are not occluded. */
+  AUG_FLAG_OCCLUDE = 2
+} aug_flags;
+
 /*
  * One volume of a batch.  Arrays of these live in DEVICE memory, so a CUDA
  * graph captured once can be replayed with new parameters written into the
@@ -88,7 +101,8 @@ typedef struct __attribute__((aligned(16))) {
   float noise_sigma;       /* standard deviation of the additive noise (>= 0)    */
   float fill_image;        /* value of every input tap outside the volume         */
   uint32_t noise_id;       /* third Philox counter word (usually the batch index) */
-  uint32_t reserved[3];    /* must be zero                                        */
+  uint32_t flags;          /* aug_flags bits (0: plain warp + affine + noise)     */
+  float occ_z0, occ_dz;    /* occlusion slab (AUG_FLAG_OCCLUDE), occ_dz >= 0       */
 } aug_volume_desc;
 
 /* ---- workspace ----------------------------------------------------------
@@ -153,8 +167,10 @@ aug_status aug_warp_fwd_volume(const aug_volume_desc* h_desc, uint64_t seed,
  *             order may differ.
  * d_grad_affine: [n_vols][12] float32, or NULL to skip; overwritten;
  *             reduced in a fixed order (bitwise reproducible).
- * Errors as aug_warp_fwd; an int16 volume with d_grad_in != NULL is a
- * descriptor error. */
+ * Occluded output voxels (AUG_FLAG_OCCLUDE) pass no gradient.  A descriptor
+ * with AUG_FLAG_WINDOW (the clamp has no useful adjoint here) and an int16
+ * volume with d_grad_in != NULL are descriptor errors.  Other errors as
+ * aug_warp_fwd. */
 aug_status aug_warp_bwd(const aug_volume_desc* d_descs, int n_vols,
                         const float* const* d_grad_out, float* const* d_grad_in,
                         float* d_grad_affine, void* d_workspace, size_t workspace_bytes,

@@ -24,16 +24,18 @@ LIB_PATH = os.path.join(_HERE, "libaugwarp.so")
 AUG_OK, AUG_ERR_INVALID_ARG, AUG_ERR_CUDA, AUG_ERR_WORKSPACE, AUG_ERR_DESCRIPTOR, \
     AUG_ERR_UNSUPPORTED = range(6)
 AUG_F32, AUG_I16 = 0, 1
+AUG_FLAG_WINDOW, AUG_FLAG_OCCLUDE = 1, 2
 OP_FWD, OP_BWD, OP_IOU = 0, 1, 2
 
 # Layout of aug_volume_desc (144 bytes, 16-byte aligned).
 DESC_DTYPE = np.dtype({
     "names": ["image", "label", "out_image", "out_label", "in_nx", "in_ny", "in_nz",
               "image_dtype", "out_nx", "out_ny", "out_nz", "fill_label", "affine", "photo_a",
-              "photo_b", "noise_sigma", "fill_image", "noise_id", "reserved"],
+              "photo_b", "noise_sigma", "fill_image", "noise_id", "flags", "occ_z0", "occ_dz"],
     "formats": ["<u8", "<u8", "<u8", "<u8", "<i4", "<i4", "<i4", "<i4", "<i4", "<i4", "<i4",
-                "<i4", ("<f4", (12,)), "<f4", "<f4", "<f4", "<f4", "<u4", ("<u4", (3,))],
-    "offsets": [0, 8, 16, 24, 32, 36, 40, 44, 48, 52, 56, 60, 64, 112, 116, 120, 124, 128, 132],
+                "<i4", ("<f4", (12,)), "<f4", "<f4", "<f4", "<f4", "<u4", "<u4", "<f4", "<f4"],
+    "offsets": [0, 8, 16, 24, 32, 36, 40, 44, 48, 52, 56, 60, 64, 112, 116, 120, 124, 128, 132,
+                136, 140],
     "itemsize": 144,
 })
 
@@ -238,7 +240,7 @@ class VolumeBatch:
     def __init__(self, images: Sequence[Optional[torch.Tensor]], affines, out_shapes,
                  labels=None, out_images=None, out_labels=None, photo_a=None, photo_b=None,
                  noise_sigma=None, fill_image=-1000.0, fill_label=0, noise_ids=None,
-                 device=None):
+                 flags=None, occ_z0=None, occ_dz=None, device=None):
         B = len(out_shapes)
         self.n = B
         h = np.zeros(B, DESC_DTYPE)
@@ -284,6 +286,12 @@ class VolumeBatch:
         h["affine"] = aff
         h["photo_a"], h["photo_b"], h["noise_sigma"] = pa, pb, ns
         h["fill_image"], h["fill_label"], h["noise_id"] = fi, fl, nid
+        if flags is not None:
+            h["flags"] = np.asarray(flags, np.uint32)
+        if occ_z0 is not None:
+            h["occ_z0"] = np.asarray(occ_z0, np.float32)
+        if occ_dz is not None:
+            h["occ_dz"] = np.asarray(occ_dz, np.float32)
         self.h_descs = h
         dev = device or (images[0].device if images[0] is not None else torch.device("cuda"))
         self.d_descs = torch.from_numpy(h.view(np.uint8).copy()).to(dev)

@@ -63,11 +63,13 @@ int persistent_grid(const void* kernel, int block, size_t smem) {
 
 __global__ void k_prepare(const aug_volume_desc* __restrict__ descs, int n_vols, int need,
                           int f32_only, const float* const* gout, float* const* gin,
-                          int need_label, VolConst* __restrict__ tab, WsHeader* ws) {
+                          int need_label, unsigned forbid_flags, VolConst* __restrict__ tab,
+                          WsHeader* ws) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
   if (v >= n_vols) return;
   const aug_volume_desc d = descs[v];
   bool ok = desc_valid(d, needs_image(d, need), f32_only != 0);
+  ok &= (d.flags & forbid_flags) == 0u;
   if (gout != nullptr) ok &= gout[v] != nullptr;
   if (gin != nullptr) ok &= gin[v] != nullptr;
   if (need_label) ok &= d.label != nullptr;
@@ -80,8 +82,10 @@ __global__ void k_prepare(const aug_volume_desc* __restrict__ descs, int n_vols,
 cudaError_t launch_prepare(const aug_volume_desc* d, int n, int need, bool f32_only,
                            const float* const* gout, float* const* gin, bool need_label,
                            VolConst* tab, WsHeader* ws, cudaStream_t st) {
+  // The adjoint (need == NEED_IMAGE_ALWAYS) has no adjoint of the window clamp.
+  const unsigned forbid = need == NEED_IMAGE_ALWAYS ? (unsigned)AUG_FLAG_WINDOW : 0u;
   k_prepare<<<(n + 127) / 128, 128, 0, st>>>(d, n, need, f32_only ? 1 : 0, gout, gin,
-                                              need_label ? 1 : 0, tab, ws);
+                                              need_label ? 1 : 0, forbid, tab, ws);
   return cudaGetLastError();
 }
 
@@ -182,7 +186,8 @@ bool host_desc_ok(const aug_volume_desc& d) {
   if (!isfinite(d.photo_a) || !isfinite(d.photo_b) || !isfinite(d.noise_sigma) ||
       d.noise_sigma < 0.0f || !isfinite(d.fill_image))
     return false;
-  if (d.reserved[0] || d.reserved[1] || d.reserved[2]) return false;
+  if (d.flags & ~(unsigned)(AUG_FLAG_WINDOW | AUG_FLAG_OCCLUDE)) return false;
+  if (!isfinite(d.occ_z0) || !isfinite(d.occ_dz) || d.occ_dz < 0.0f) return false;
   if (d.out_image != nullptr &&
       (d.image == nullptr || (d.image_dtype != AUG_F32 && d.image_dtype != AUG_I16)))
     return false;

@@ -39,6 +39,7 @@ __device__ __forceinline__ void bwd_run(const VolConst& vc, const TileCoord& tc,
   const int nx = vc.nx, ny = vc.ny, nz = vc.nz, nxy = nx * ny;
   const int plane = vc.onx * vc.ony;
   const float a = vc.a, fill = vc.fill;
+  const int klo = vc.occ_klo, khi = vc.occ_khi;
   int o = (tc.k0 * vc.ony + tc.jc) * vc.onx + tc.ic;
   // Interior runs merge along z: when the next voxel's cell is the current
   // one moved by +1 in z, the four z+1 contributions of this voxel land on the
@@ -51,7 +52,9 @@ __device__ __forceinline__ void bwd_run(const VolConst& vc, const TileCoord& tc,
 #define RADD(p, v) (SMEM ? red_add_shared((p), (v)) : red_add_global((p), (v)))
 #pragma unroll 4
   for (int k = tc.k0; k < tc.k1; ++k) {
-    const float ga = tc.valid ? a * __ldcs(g + o) : 0.0f;
+    // An occluded output voxel is the constant 0: no gradient flows through it.
+    const bool occ = k >= klo && k <= khi;
+    const float ga = (tc.valid && !occ) ? a * __ldcs(g + o) : 0.0f;
     Taps t;
     load_taps<TIn, MODE>(img, sx, sy, sz, nx, ny, nz, fill, t);
     if (GIN && tc.valid) {

@@ -44,6 +44,8 @@ struct VolConst {
   float a, b, sigma, fill;
   unsigned noise_id;
   int ok;
+  int flags;             // AUG_FLAG_* bits
+  int occ_klo, occ_khi;  // occluded output z indices k_lo <= k <= k_hi (empty if k_lo > k_hi)
 };
 
 // Full check of one descriptor (pure).  need_image: an image of a known
@@ -64,7 +66,8 @@ __device__ inline bool desc_valid(const aug_volume_desc& d, bool need_image, boo
   }
   ok &= isfinite(d.photo_a) && isfinite(d.photo_b) && isfinite(d.noise_sigma) &&
         d.noise_sigma >= 0.0f && isfinite(d.fill_image);
-  ok &= d.reserved[0] == 0u && d.reserved[1] == 0u && d.reserved[2] == 0u;
+  ok &= (d.flags & ~(unsigned)(AUG_FLAG_WINDOW | AUG_FLAG_OCCLUDE)) == 0u;
+  ok &= isfinite(d.occ_z0) && isfinite(d.occ_dz) && d.occ_dz >= 0.0f;
   if (need_image) {
     ok &= d.image != nullptr && (d.image_dtype == AUG_F32 || d.image_dtype == AUG_I16);
     if (f32_only) ok &= d.image_dtype == AUG_F32;
@@ -99,6 +102,15 @@ __device__ inline void make_volconst(const aug_volume_desc& d, bool ok, VolConst
   vc.sigma = d.noise_sigma;
   vc.fill = d.fill_image;
   vc.noise_id = d.noise_id;
+  vc.flags = (int)d.flags;
+  // z0 <= k <= z0 + dz over integers k, decided in double exactly as written.
+  vc.occ_klo = 1;
+  vc.occ_khi = 0;
+  if ((d.flags & AUG_FLAG_OCCLUDE) && isfinite(d.occ_z0) && isfinite(d.occ_dz)) {
+    const double lo = ceil((double)d.occ_z0), hi = floor((double)d.occ_z0 + (double)d.occ_dz);
+    vc.occ_klo = (int)fmin(fmax(lo, -1.0), 1073741824.0);
+    vc.occ_khi = (int)fmin(fmax(hi, -2.0), 1073741824.0);
+  }
   vc.ok = ok ? 1 : 0;
 }
 

@@ -29,18 +29,28 @@ struct FwdP {
   long long dx, dy, dz;
   int nx, ny, nz, nxy, plane, fill_label;
   float a, b, sigma, fill, yfill;  // yfill = a * fill + b
+  int klo, khi;                    // occluded output z indices (empty if klo > khi)
+  bool window;                     // clamp the output to [0, 1] after the noise
 };
+
+// Final value of one output voxel: occluded voxels are exactly 0 (nothing
+// after the warp applies to them); otherwise the optional window clamp.
+template <typename TIn>
+__device__ __forceinline__ float finish(const FwdP<TIn>& P, int k, float y) {
+  if (k >= P.klo && k <= P.khi) return 0.0f;
+  return P.window ? __saturatef(y) : y;
+}
 
 // Exterior quad: every tap reads the fill value, so the sample is constant;
 // only the noise differs per voxel.  The coordinate advances by n steps at once.
 template <typename TIn, bool IMG, bool LAB>
 __device__ __forceinline__ void fwd_quad_exterior(const FwdP<TIn>& P, int& o, int n, bool valid,
-                                                  const float z[4]) {
+                                                  const float z[4], int kq) {
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
     if (m < n) {
       if (valid) {
-        if (IMG) __stcs(P.oimg + o, fmaf(P.sigma, z[m], P.yfill));
+        if (IMG) __stcs(P.oimg + o, finish(P, kq + m, fmaf(P.sigma, z[m], P.yfill)));
         if (LAB) P.olab[o] = (uint8_t)P.fill_label;
       }
       o += P.plane;
@@ -58,7 +68,7 @@ template <typename TIn, int MODE, bool IMG, bool LAB, bool FULL, int PD>
 __device__ __forceinline__ void fwd_quad(const FwdP<TIn>& P, long long& sx, long long& sy,
                                          long long& sz, int& o, int n, bool valid,
                                          bool noisy, unsigned long long quad, unsigned noise_id,
-                                         unsigned key0, unsigned key1) {
+                                         unsigned key0, unsigned key1, int kq) {
   float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
   for (int g0 = 0; g0 < 4; g0 += PD) {
@@ -75,6 +85,8 @@ __device__ __forceinline__ void fwd_quad(const FwdP<TIn>& P, long long& sx, long
       if (FULL || m < n) {
         const int fx = q40_floor(sx), fy = q40_floor(sy), fz = q40_floor(sz);
         const int hbx = q40_halfbit(sx), hby = q40_halfbit(sy), hbz = q40_halfbit(sz);
+        // An occluded voxel skips the image fetch (warp-uniform: one k per warp).
+        const bool fetch = !(kq + m >= P.klo && kq + m <= P.khi);
         if (IMG) {
           w[i][0] = q40_frac(sx);
           w[i][1] = q40_frac(sy);
@@ -82,7 +94,7 @@ __device__ __forceinline__ void fwd_quad(const FwdP<TIn>& P, long long& sx, long
         }
         if (MODE == MODE_INTERIOR) {
           const int base = (fz * P.ny + fy) * P.nx + fx;
-          if (IMG) {
+          if (IMG && fetch) {
             const TIn* p = P.img + base;
             tap[i][0] = ld_val(p);
             tap[i][1] = ld_val(p + 1);
@@ -95,7 +107,7 @@ __device__ __forceinline__ void fwd_quad(const FwdP<TIn>& P, long long& sx, long
           }
           if (LAB) lab[i] = __ldg(P.lab + (base + hbx + hby * P.nx + hbz * P.nxy));
         } else {
-          if (IMG) {
+          if (IMG && fetch) {
             const bool x0 = (unsigned)fx < (unsigned)P.nx,
                        x1 = (unsigned)(fx + 1) < (unsigned)P.nx;
             const bool y0 = (unsigned)fy < (unsigned)P.ny,
@@ -150,6 +162,8 @@ __device__ __forceinline__ void fwd_quad(const FwdP<TIn>& P, long long& sx, long
                              fma2(pk2(P.a, P.a), v, pk2(P.b, P.b)));
         float y0, y1;
         upk2(y, y0, y1);
+        y0 = finish(P, kq + m, y0);
+        y1 = finish(P, kq + m + 1, y1);
         if (valid) {
           __stcs(P.oimg + o, y0);
           if (LAB) P.olab[o] = (uint8_t)lab[i];
@@ -173,7 +187,7 @@ __device__ __forceinline__ void fwd_quad(const FwdP<TIn>& P, long long& sx, long
           const float c0 = fmaf(ty, c10 - c00, c00);
           const float c1 = fmaf(ty, c11 - c01, c01);
           const float v = fmaf(tz, c1 - c0, c0);
-          if (valid) __stcs(P.oimg + o, fmaf(P.sigma, z[m], fmaf(P.a, v, P.b)));
+          if (valid) __stcs(P.oimg + o, finish(P, kq + m, fmaf(P.sigma, z[m], fmaf(P.a, v, P.b))));
         }
         if (LAB && valid) P.olab[o] = (uint8_t)lab[i];
         o += P.plane;
@@ -205,6 +219,9 @@ __device__ __forceinline__ void fwd_tile_t(const VolConst& vc, int t, unsigned k
   P.sigma = vc.sigma;
   P.fill = vc.fill;
   P.yfill = fmaf(vc.a, vc.fill, vc.b);
+  P.klo = vc.occ_klo;
+  P.khi = vc.occ_khi;
+  P.window = (vc.flags & AUG_FLAG_WINDOW) != 0;
   const unsigned noise_id = vc.noise_id;
   const bool noisy = IMG && vc.sigma > 0.0f;
   const unsigned onx = (unsigned)vc.onx, ony = (unsigned)vc.ony;
@@ -227,7 +244,7 @@ __device__ __forceinline__ void fwd_tile_t(const VolConst& vc, int t, unsigned k
         quad_normals(((unsigned long long)(kq >> 2) * ony + (unsigned)tc.jc) * onx +
                          (unsigned)tc.ic,
                      noise_id, key0, key1, z);
-      fwd_quad_exterior<TIn, IMG, LAB>(P, o, n, tc.valid, z);
+      fwd_quad_exterior<TIn, IMG, LAB>(P, o, n, tc.valid, z, kq);
     }
     return;
   }
@@ -237,7 +254,7 @@ __device__ __forceinline__ void fwd_tile_t(const VolConst& vc, int t, unsigned k
       const unsigned long long quad =
           ((unsigned long long)(kq >> 2) * ony + (unsigned)tc.jc) * onx + (unsigned)tc.ic;
       fwd_quad<TIn, MODE_INTERIOR, IMG, LAB, true, PD>(P, sx, sy, sz, o, 4, tc.valid, noisy, quad,
-                                                       noise_id, key0, key1);
+                                                       noise_id, key0, key1, kq);
     }
     return;
   }
@@ -253,20 +270,20 @@ __device__ __forceinline__ void fwd_tile_t(const VolConst& vc, int t, unsigned k
     if (mode == MODE_EXTERIOR) {
       float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
       if (noisy) quad_normals(quad, noise_id, key0, key1, z);
-      fwd_quad_exterior<TIn, IMG, LAB>(P, o, n, tc.valid, z);
+      fwd_quad_exterior<TIn, IMG, LAB>(P, o, n, tc.valid, z, kq);
       sx += (long long)n * P.dx;
       sy += (long long)n * P.dy;
       sz += (long long)n * P.dz;
     } else if (n == 4) {
       if (mode == MODE_INTERIOR)
         fwd_quad<TIn, MODE_INTERIOR, IMG, LAB, true, PD>(P, sx, sy, sz, o, 4, tc.valid, noisy, quad,
-                                                     noise_id, key0, key1);
+                                                     noise_id, key0, key1, kq);
       else
         fwd_quad<TIn, MODE_GENERAL, IMG, LAB, true, PD>(P, sx, sy, sz, o, 4, tc.valid, noisy, quad,
-                                                    noise_id, key0, key1);
+                                                    noise_id, key0, key1, kq);
     } else {
       fwd_quad<TIn, MODE_GENERAL, IMG, LAB, false, PD>(P, sx, sy, sz, o, n, tc.valid, noisy, quad,
-                                                   noise_id, key0, key1);
+                                                   noise_id, key0, key1, kq);
     }
   }
 }

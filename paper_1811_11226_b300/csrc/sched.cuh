@@ -114,6 +114,7 @@ __device__ __forceinline__ bool needs_image(const aug_volume_desc& d, int need) 
 // read a tile's constants straight from that table (L1-cached, no barrier).
 __global__ void k_prepare(const aug_volume_desc* __restrict__ descs, int n_vols, int need,
                           int f32_only, const float* const* gout, float* const* gin,
-                          int need_label, VolConst* __restrict__ tab, WsHeader* ws);
+                          int need_label, unsigned forbid_flags, VolConst* __restrict__ tab,
+                          WsHeader* ws);
 
 }  // namespace augk

@@ -46,7 +46,10 @@ def batch_for(cases, with_image=True, with_label=True):
                           noise_sigma=[v.sigma for v in cases],
                           fill_image=[v.fill_image for v in cases],
                           fill_label=[v.fill_label for v in cases],
-                          noise_ids=[v.noise_id for v in cases])
+                          noise_ids=[v.noise_id for v in cases],
+                          flags=[getattr(v, "flags", 0) for v in cases],
+                          occ_z0=[getattr(v, "occ_z0", 0.0) for v in cases],
+                          occ_dz=[getattr(v, "occ_dz", 0.0) for v in cases])
     return batch, outs_i, outs_l
 
 
@@ -72,12 +75,14 @@ def run_fwd(cases, seed, batched=True, variant=None):
             [None if t is None else t.cpu().numpy() for t in ol])
 
 
-def check_image(gpu, ref, what=""):
+def check_image(gpu, ref, what="", tol=IMG_TOL):
+    """Image parity; ``tol`` defaults to 2e-3 HU (scale it by the intensity
+    affine's slope for window/level outputs in [0, 1])."""
     assert gpu.shape == ref.shape
     assert np.all(np.isfinite(gpu)), f"{what}: non-finite output"
     err = np.abs(gpu.astype(np.float64) - ref)
     worst = float(err.max()) if err.size else 0.0
-    assert worst <= IMG_TOL, f"{what}: max |gpu - oracle| = {worst:.3e} HU"
+    assert worst <= tol, f"{what}: max |gpu - oracle| = {worst:.3e} (tolerance {tol:.1e})"
     return worst
 
 
