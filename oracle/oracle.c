@@ -43,6 +43,7 @@
  */
 #include <math.h>
 #include <stddef.h>
+#include <stdlib.h>
 #include <stdint.h>
 #include <string.h>
 
@@ -390,4 +391,87 @@ ORACLE_EXPORT void oracle_iou(const float* p, const uint8_t* y, int n_classes, i
       }
     }
   }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Loss variants of Sec. 5.C on one volume, same layouts as oracle_iou:       */
+/*   kind 0  IOU     L = 1 - I/U,            U = P + Y - I                    */
+/*   kind 1  Dice    L = 1 - 2I/(P + Y)                                       */
+/*   kind 2  IOU^m   as IOU with every p_k replaced by q_k = p_k^m (m > 0)    */
+/* with I = sum q y, P = sum q, Y = sum y (q = p for kinds 0 and 1), and a    */
+/* zero denominator giving loss 0 and gradient 0.  Gradients:                 */
+/*   IOU    dL/dq_k = y_k ? -1/U : I/U^2                                      */
+/*   Dice   dL/dq_k = (2I - 2 y_k (P + Y)) / (P + Y)^2                        */
+/*   IOU^m  dL/dp_k = m p_k^(m-1) dL/dq_k                                     */
+/* With logits != 0 the input x holds per-voxel class scores and             */
+/* p_{c,k} = exp(x_{c,k}) / sum_j exp(x_{j,k}) (softmax over the classes);    */
+/* the gradient is then taken with respect to x:                              */
+/*   dL/dx_{c,k} = p_{c,k} (g_{c,k} - sum_j p_{j,k} g_{j,k}),  g = dL/dp.      */
+/* L here is the batch-level mean over classes, so the class terms of the    */
+/* softmax chain rule add up across classes.                                  */
+/* ------------------------------------------------------------------------ */
+ORACLE_EXPORT void oracle_loss(const float* x, const uint8_t* y, int n_classes, int64_t nvox,
+                               int kind, double m, int logits, double grad_scale,
+                               double* loss_c, double* sums, double* grad) {
+  const size_t n = (size_t)n_classes * (size_t)nvox;
+  double* p = (double*)malloc(n * sizeof(double));
+  double* g = (double*)malloc(n * sizeof(double));
+  for (int64_t k = 0; k < nvox; ++k) {
+    if (logits) {
+      double mx = -INFINITY, z = 0.0;
+      for (int c = 0; c < n_classes; ++c) mx = fmax(mx, (double)x[(size_t)c * nvox + k]);
+      for (int c = 0; c < n_classes; ++c) z += exp((double)x[(size_t)c * nvox + k] - mx);
+      for (int c = 0; c < n_classes; ++c)
+        p[(size_t)c * nvox + k] = exp((double)x[(size_t)c * nvox + k] - mx) / z;
+    } else {
+      for (int c = 0; c < n_classes; ++c) p[(size_t)c * nvox + k] = (double)x[(size_t)c * nvox + k];
+    }
+  }
+  for (int c = 0; c < n_classes; ++c) {
+    const double* pc = p + (size_t)c * (size_t)nvox;
+    double I = 0.0, P = 0.0, Y = 0.0;
+    for (int64_t k = 0; k < nvox; ++k) {
+      double q = (kind == 2) ? pow(pc[k], m) : pc[k];
+      double yk = (y[k] == c) ? 1.0 : 0.0;
+      I += q * yk;
+      P += q;
+      Y += yk;
+    }
+    double den = (kind == 1) ? P + Y : P + Y - I;
+    double l = 0.0;
+    if (den > 0.0) l = (kind == 1) ? 1.0 - 2.0 * I / den : 1.0 - I / den;
+    loss_c[c] = l;
+    if (sums) {
+      sums[3 * c + 0] = I;
+      sums[3 * c + 1] = P;
+      sums[3 * c + 2] = Y;
+    }
+    double* gc = g + (size_t)c * (size_t)nvox;
+    for (int64_t k = 0; k < nvox; ++k) {
+      double d = 0.0;
+      int yk = y[k] == c;
+      if (den > 0.0) {
+        if (kind == 1)
+          d = (2.0 * I - (yk ? 2.0 * den : 0.0)) / (den * den);
+        else
+          d = yk ? -1.0 / den : I / (den * den);
+        if (kind == 2) d *= m * pow(pc[k], m - 1.0);
+      }
+      gc[k] = grad_scale * d;
+    }
+  }
+  if (grad) {
+    for (int64_t k = 0; k < nvox; ++k) {
+      double dot = 0.0;
+      if (logits)
+        for (int c = 0; c < n_classes; ++c)
+          dot += p[(size_t)c * nvox + k] * g[(size_t)c * nvox + k];
+      for (int c = 0; c < n_classes; ++c) {
+        const size_t i = (size_t)c * nvox + k;
+        grad[i] = logits ? p[i] * (g[i] - dot) : g[i];
+      }
+    }
+  }
+  free(p);
+  free(g);
 }

@@ -39,6 +39,8 @@ def lib():
             L.oracle_warp_bwd.argtypes = [_vp, _int, _i64, _i64, _i64, _i64, _i64, _i64, _vp,
                                           _f32, _f32, _int, _f32, _f32, _vp, _vp, _vp, _vp]
             L.oracle_iou.argtypes = [_vp, _vp, _int, _i64, C.c_double, _vp, _vp, _vp]
+            L.oracle_loss.argtypes = [_vp, _vp, _int, _i64, _int, C.c_double, _int,
+                                      C.c_double, _vp, _vp, _vp]
             _lib = L
     return _lib
 
@@ -179,3 +181,45 @@ def warp_iou(vols, p_packed, n_classes: int, want_grad=True):
         off += n_classes * nvox
     grad = np.concatenate(grads) if want_grad else None
     return np.asarray(losses), grad, np.asarray(sums)
+
+
+LOSS_IOU, LOSS_DICE, LOSS_IOU_POW = 0, 1, 2
+
+
+def loss(x, y, n_classes: int, kind: int = LOSS_IOU, m: float = 1.0, logits: bool = False,
+         grad_scale: float = 1.0, want_grad=True):
+    """Loss variant `kind` of one volume (IOU, Dice, IOU with p^m), on
+    probabilities or (``logits``) on class scores through a softmax; the
+    gradient is with respect to the input x.  Layout as iou()."""
+    x = _np(x, np.float32).reshape(n_classes, -1)
+    y = _np(y, np.uint8).reshape(-1)
+    nvox = y.size
+    lossc = np.empty(n_classes, np.float64)
+    sums = np.empty((n_classes, 3), np.float64)
+    grad = np.empty((n_classes, nvox), np.float64) if want_grad else None
+    lib().oracle_loss(_ptr(x), _ptr(y), n_classes, nvox, int(kind), C.c_double(m), int(logits),
+                      C.c_double(grad_scale), _ptr(lossc), _ptr(sums), _ptr(grad))
+    return lossc, sums, grad
+
+
+def warp_loss(vols, x_packed, n_classes: int, kind: int = LOSS_IOU, m: float = 1.0,
+              logits: bool = False, want_grad=True):
+    """Label warp + loss variant, batch-averaged (as warp_iou, same return
+    triple); with ``logits`` the gradient is with respect to the class scores."""
+    x = _np(x_packed, np.float32).reshape(-1)
+    B = len(vols)
+    scale = 1.0 / (B * n_classes)
+    losses, sums, grads = [], [], []
+    off = 0
+    for v in vols:
+        nvox = v.n_out
+        _, lab, _, _ = warp_fwd(v, 0, want_image=False, want_label=True)
+        xc = x[off: off + n_classes * nvox].reshape(n_classes, nvox)
+        lc, sc, gc = loss(xc, lab.reshape(-1), n_classes, kind, m, logits, scale, want_grad)
+        losses.append(lc.mean())
+        sums.append(sc)
+        if want_grad:
+            grads.append(gc.reshape(-1))
+        off += n_classes * nvox
+    return (np.asarray(losses), (np.concatenate(grads) if want_grad else None),
+            np.stack(sums))
