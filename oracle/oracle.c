@@ -394,15 +394,15 @@ ORACLE_EXPORT void oracle_iou(const float* p, const uint8_t* y, int n_classes, i
 }
 
 /* ------------------------------------------------------------------------ */
-/* Loss variants of Sec. 5.C on one volume, same layouts as oracle_iou:       */
+/* Loss variants of Sec. 5.C on one volume, same layouts as oracle_iou, with  */
+/* q_k = p_k^m (m > 0; q = p for m = 1, the L^m family of Sec. 5.C):          */
 /*   kind 0  IOU     L = 1 - I/U,            U = P + Y - I                    */
 /*   kind 1  Dice    L = 1 - 2I/(P + Y)                                       */
-/*   kind 2  IOU^m   as IOU with every p_k replaced by q_k = p_k^m (m > 0)    */
-/* with I = sum q y, P = sum q, Y = sum y (q = p for kinds 0 and 1), and a    */
-/* zero denominator giving loss 0 and gradient 0.  Gradients:                 */
+/* with I = sum q y, P = sum q, Y = sum y, and a zero denominator giving     */
+/* loss 0 and gradient 0.  Gradients:                                         */
 /*   IOU    dL/dq_k = y_k ? -1/U : I/U^2                                      */
 /*   Dice   dL/dq_k = (2I - 2 y_k (P + Y)) / (P + Y)^2                        */
-/*   IOU^m  dL/dp_k = m p_k^(m-1) dL/dq_k                                     */
+/*   dL/dp_k = m p_k^(m-1) dL/dq_k                                            */
 /* With logits != 0 the input x holds per-voxel class scores and             */
 /* p_{c,k} = exp(x_{c,k}) / sum_j exp(x_{j,k}) (softmax over the classes);    */
 /* the gradient is then taken with respect to x:                              */
@@ -431,7 +431,7 @@ ORACLE_EXPORT void oracle_loss(const float* x, const uint8_t* y, int n_classes, 
     const double* pc = p + (size_t)c * (size_t)nvox;
     double I = 0.0, P = 0.0, Y = 0.0;
     for (int64_t k = 0; k < nvox; ++k) {
-      double q = (kind == 2) ? pow(pc[k], m) : pc[k];
+      double q = (m == 1.0) ? pc[k] : pow(pc[k], m);
       double yk = (y[k] == c) ? 1.0 : 0.0;
       I += q * yk;
       P += q;
@@ -455,7 +455,7 @@ ORACLE_EXPORT void oracle_loss(const float* x, const uint8_t* y, int n_classes, 
           d = (2.0 * I - (yk ? 2.0 * den : 0.0)) / (den * den);
         else
           d = yk ? -1.0 / den : I / (den * den);
-        if (kind == 2) d *= m * pow(pc[k], m - 1.0);
+        if (m != 1.0) d *= m * pow(pc[k], m - 1.0);
       }
       gc[k] = grad_scale * d;
     }

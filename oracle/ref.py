@@ -183,12 +183,12 @@ def warp_iou(vols, p_packed, n_classes: int, want_grad=True):
     return np.asarray(losses), grad, np.asarray(sums)
 
 
-LOSS_IOU, LOSS_DICE, LOSS_IOU_POW = 0, 1, 2
+LOSS_IOU, LOSS_DICE = 0, 1
 
 
 def loss(x, y, n_classes: int, kind: int = LOSS_IOU, m: float = 1.0, logits: bool = False,
          grad_scale: float = 1.0, want_grad=True):
-    """Loss variant `kind` of one volume (IOU, Dice, IOU with p^m), on
+    """Loss `kind` (IOU or Dice) of one volume with p replaced by p^m, on
     probabilities or (``logits``) on class scores through a softmax; the
     gradient is with respect to the input x.  Layout as iou()."""
     x = _np(x, np.float32).reshape(n_classes, -1)

@@ -4,8 +4,9 @@
   binary p (set operations);
 * the paper's counter-example p = (0, 1), y = (1, 0) violates the triangle
   inequality for Dice (but not for IOU);
-* IOU^m equals IOU for m = 1 and for binary p (property 1), differs for
-  fractional p, and is monotone in each p_k (property 2);
+* IOU^m and Dice^m equal IOU and Dice for m = 1 and for binary p
+  (property 1), differ for fractional p, and are monotone in each p_k
+  (property 2);
 * every gradient matches FP64 central differences.
 """
 import numpy as np
@@ -44,29 +45,32 @@ def test_dice_counterexample_to_triangle_inequality():
     assert d(p, y, ref.LOSS_IOU) <= d(p, u, ref.LOSS_IOU) + d(y, u, ref.LOSS_IOU)
 
 
-def test_iou_power_reduces_to_iou():
+@pytest.mark.parametrize("kind", [ref.LOSS_IOU, ref.LOSS_DICE])
+def test_power_family_reduces_on_binary_inputs(kind):
     rng = np.random.default_rng(1)
     y = rng.random(200) < 0.3
     p = rng.random(200).astype(np.float32)
-    l1, g1 = one(p, y, ref.LOSS_IOU_POW, 1.0)
-    l0, g0 = one(p, y, ref.LOSS_IOU)
-    assert abs(l1 - l0) < 1e-15 and np.allclose(g1, g0, rtol=1e-14, atol=0)
     pb = (rng.random(200) < 0.4).astype(np.float32)
-    for m in (2.0, 3.5):
-        assert abs(one(pb, y, ref.LOSS_IOU_POW, m)[0] - one(pb, y, ref.LOSS_IOU)[0]) < 1e-15
-    assert one(p, y, ref.LOSS_IOU_POW, 2.0)[0] != one(p, y, ref.LOSS_IOU)[0]
-    _, g = one(p, y, ref.LOSS_IOU_POW, 2.0)
-    assert np.all(g[y] <= 0) and np.all(g[~y] >= 0)
+    base = one(pb, y, kind)[0]
+    binary = np.sum((pb > 0) & y), np.sum(pb > 0), np.sum(y)
+    exact = (1 - binary[0] / (binary[1] + binary[2] - binary[0]) if kind == 0
+             else 1 - 2 * binary[0] / (binary[1] + binary[2]))
+    assert abs(base - exact) < 1e-15
+    for m in (0.5, 2.0, 3.5):
+        assert abs(one(pb, y, kind, m)[0] - base) < 1e-15
+        assert one(p, y, kind, m)[0] != one(p, y, kind)[0]
+        _, g = one(p, y, kind, m)
+        assert np.all(g[y] <= 0) and np.all(g[~y] >= 0)
 
 
-@pytest.mark.parametrize("kind,m", [(1, 1.0), (2, 2.0), (2, 1.5)])
+@pytest.mark.parametrize("kind,m", [(1, 1.0), (0, 2.0), (0, 1.5), (1, 0.5), (1, 3.0)])
 def test_variant_gradients_match_central_differences(kind, m):
     rng = np.random.default_rng(2 + kind)
     n = 40
     y = rng.random(n) < 0.5
     p = (0.05 + 0.9 * rng.random(n)).astype(np.float32)
     _, g = one(p, y, kind, m)
-    h = np.float32(2.0 ** -12)
+    h = np.float32(2.0 ** -14)
     for k in range(n):
         pp, pm = p.copy(), p.copy()
         pp[k] += h
@@ -95,13 +99,13 @@ def test_logits_of_log_probabilities_give_the_probability_loss():
     x = np.log(p).astype(np.float32)
     p32 = np.exp(x.astype(np.float64))
     p32 = (p32 / p32.sum(0)).astype(np.float32)
-    for kind, m in [(0, 1.0), (1, 1.0), (2, 2.5)]:
+    for kind, m in [(0, 1.0), (1, 1.0), (0, 2.5), (1, 0.7)]:
         lz, sz, _ = ref.loss(x, y, C, kind, m, logits=True)
         lp, sp, _ = ref.loss(p32, y, C, kind, m)
         assert np.max(np.abs(lz - lp)) < 1e-6 and np.max(np.abs(sz - sp)) < 1e-3
 
 
-@pytest.mark.parametrize("kind,m", [(0, 1.0), (1, 1.0), (2, 3.0)])
+@pytest.mark.parametrize("kind,m", [(0, 1.0), (1, 1.0), (0, 3.0), (1, 0.6)])
 def test_logit_gradient_is_shift_invariant_and_matches_differences(kind, m):
     """Adding one constant to all class scores of a voxel leaves the softmax
     and so the loss unchanged, hence the gradient sums to 0 over classes;
