@@ -362,6 +362,8 @@ def run_ours(args, rank, world, local):
         res["fwd_bwd"] = bench_fwd_bwd(args, A, D, dev, stream, seed, world)
     if (args.only == "all" and args.all) or args.only == "iou":
         res["iou"] = bench_iou(args, A, dev, stream)
+    if (args.only == "all" and args.all) or args.only == "loss":
+        res["loss_variants"] = bench_loss_variants(args, A, dev, stream)
     if (args.only == "all" and args.all) or args.only == "train":
         res["train_step"] = bench_train(args, A, dev, stream, seed)
     res["peak"], res["peak_kind"] = peak, peak_kind
@@ -426,6 +428,38 @@ def bench_iou(args, A, dev, stream):
     return {"value": round(n_out / (ms * 1e-3) / 1e9, 3), "unit": "Gvox/s",
             "ms_per_step": round(ms, 4), "alg_GBps": round(alg / (ms * 1e-3) / 1e9, 1),
             "workload": "8 x 120x120x160 label warp + IOU fwd/bwd, 6 classes"}
+
+
+def bench_loss_variants(args, A, dev, stream):
+    """Sec. 5.C loss variants on the 8 x 120x120x160 workload: Dice and the
+    p^2 family on probabilities (x read once, grad written), and both with the
+    softmax over 6 class scores fused in (scores read by both passes)."""
+    from synth import workloads
+    w = workloads.config3(device=dev)
+    vols = w.vols
+    batch = A.VolumeBatch([None] * len(vols), np.stack([v.T for v in vols]),
+                          [v.out_shape for v in vols], labels=[v.label for v in vols], device=dev)
+    ws = A.make_workspace(len(vols), 6, dev)
+    loss = torch.empty(len(vols), device=dev)
+    scores = workloads.class_logits([v.out_shape for v in vols], seed=3, device=dev)
+    gx = torch.empty_like(w.p)
+    n_out = sum(v.n_out for v in vols)
+    labs = sum(distinct_refs(v, False) for v in vols)
+    out = []
+    for name, kind, power, logits in [("dice", A.AUG_LOSS_DICE, 1.0, False),
+                                      ("iou_p2", A.AUG_LOSS_IOU, 2.0, False),
+                                      ("dice_softmax", A.AUG_LOSS_DICE, 1.0, True),
+                                      ("iou_p2_softmax", A.AUG_LOSS_IOU, 2.0, True)]:
+        x = scores if logits else w.p
+        graph = capture(lambda: A.seg_loss_fwd_bwd(batch.d_descs, batch.n, x, 6, loss, gx, ws,
+                                                   kind, power, logits), stream)
+        ms = time_graph(graph, max(3, args.steps // 5), args.warmup, stream)
+        reads = 1 if (kind == A.AUG_LOSS_DICE and power == 1.0 and not logits) else 2
+        alg = n_out * 6 * 4 * (reads + 1) + labs
+        log(f"[loss {name}] {ms:.4f} ms/step")
+        out.append({"loss": name, "value": round(n_out / (ms * 1e-3) / 1e9, 3), "unit": "Gvox/s",
+                    "ms_per_step": round(ms, 4), "alg_GBps": round(alg / (ms * 1e-3) / 1e9, 1)})
+    return out
 
 
 def bench_train(args, A, dev, stream, seed):
@@ -540,8 +574,8 @@ def main():
     ap.add_argument("--all", action="store_true", help="also time the IOU and training-step "
                     "workloads")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", choices=["all", "fwd", "fwd_bwd", "iou", "train"], default="all",
-                    help="time one workload only (profiling runs)")
+    ap.add_argument("--only", choices=["all", "fwd", "fwd_bwd", "iou", "loss", "train"],
+                    default="all", help="time one workload only (profiling runs)")
     ap.add_argument("--variant", type=int, default=-1,
                     help="fixed kernel variant instead of autotuning (profiling runs)")
     ap.add_argument("--no-preroll", action="store_true")
@@ -561,8 +595,9 @@ def main():
     if rank != 0:
         return
     if args.only != "all":
-        keep = {k: v for k, v in res.items() if k in ("fwd_bwd", "iou", "train_step", "ms",
-                                                       "value", "variant", "achieved")}
+        keep = {k: v for k, v in res.items() if k in ("fwd_bwd", "iou", "loss_variants",
+                                                       "train_step", "ms", "value", "variant",
+                                                       "achieved")}
         print(json.dumps({"profile_run": args.only, **keep}), flush=True)
         return
     cpu = None
@@ -600,9 +635,9 @@ def main():
         "clocks": res["clocks"],
         "cpu_baseline": cpu,
     }
-    if "iou" in res:
-        line["iou"] = res["iou"]
-        line["train_step"] = res["train_step"]
+    for key in ("iou", "loss_variants", "train_step"):
+        if key in res:
+            line[key] = res[key]
     print(json.dumps(line), flush=True)
 
 

@@ -195,6 +195,32 @@ aug_status iou_loss_fwd_bwd(const aug_volume_desc* d_descs, int n_vols, const fl
                             int n_classes, float* d_loss, float* d_grad_p, void* d_workspace,
                             size_t workspace_bytes, aug_stream_t stream);
 
+/* ---- overlap-loss variants (Sec. 5.C) in the same fused kernels --------------
+ * Generalises iou_loss_fwd_bwd (which is kind = AUG_LOSS_IOU, power = 1,
+ * logits = 0) to the other losses the paper discusses.  Per volume b, class c
+ * and output voxel k, with y_k = [warped label == c]:
+ *   p_k = x_k                                  (logits == 0: probabilities)
+ *   p_k = exp(x_{c,k}) / sum_j exp(x_{j,k})    (logits != 0: class scores,
+ *                                               softmax over the C classes)
+ *   q_k = p_k^power                            (the L^m family, power > 0)
+ *   I = sum q y, P = sum q, Y = sum y,
+ *   AUG_LOSS_IOU:  L_bc = 1 - I / (P + Y - I)
+ *   AUG_LOSS_DICE: L_bc = 1 - 2 I / (P + Y)
+ * (L_bc = 0 and no gradient where the denominator is 0);
+ * loss[b] = mean_c L_bc, and d_grad_x = d(mean_b loss[b]) / d x, i.e. with
+ * respect to the scores when logits != 0 (softmax chain rule included).
+ * Layouts as iou_loss_fwd_bwd (d_x, d_grad_x: [C][out_nz][out_ny][out_nx] per
+ * volume, packed).  power must be finite and > 0 (else AUG_ERR_INVALID_ARG);
+ * with power < 1 a probability of exactly 0 has an infinite derivative.
+ * p^power, exp and the reciprocal use the hardware approximations (relative
+ * error ~1e-6).  Variants and autotuning are shared with op 2. */
+typedef enum { AUG_LOSS_IOU = 0, AUG_LOSS_DICE = 1 } aug_loss_kind;
+
+aug_status seg_loss_fwd_bwd(const aug_volume_desc* d_descs, int n_vols, const float* d_x,
+                            int n_classes, int kind, float power, int logits, float* d_loss,
+                            float* d_grad_x, void* d_workspace, size_t workspace_bytes,
+                            aug_stream_t stream);
+
 /* ---- allocation-free variant of iou_loss_fwd_bwd --------------------------------
  * The paper has no counterpart to this entry point; it exists for callers
  * that must not allocate device memory: plug-ins hosted by a framework that

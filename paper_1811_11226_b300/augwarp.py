@@ -26,6 +26,7 @@ AUG_OK, AUG_ERR_INVALID_ARG, AUG_ERR_CUDA, AUG_ERR_WORKSPACE, AUG_ERR_DESCRIPTOR
 AUG_F32, AUG_I16 = 0, 1
 AUG_FLAG_WINDOW, AUG_FLAG_OCCLUDE = 1, 2
 OP_FWD, OP_BWD, OP_IOU = 0, 1, 2
+AUG_LOSS_IOU, AUG_LOSS_DICE = 0, 1
 
 # Layout of aug_volume_desc (144 bytes, 16-byte aligned).
 DESC_DTYPE = np.dtype({
@@ -66,6 +67,8 @@ def _load():
     L.aug_warp_bwd.restype = i32
     L.iou_loss_fwd_bwd.argtypes = [vp, i32, vp, i32, vp, vp, vp, sz, vp]
     L.iou_loss_fwd_bwd.restype = i32
+    L.seg_loss_fwd_bwd.argtypes = [vp, i32, vp, i32, i32, C.c_float, i32, vp, vp, vp, sz, vp]
+    L.seg_loss_fwd_bwd.restype = i32
     L.iou_loss_fwd_bwd_noalloc.argtypes = [vp, i32, vp, i32, vp, vp, vp, vp]
     L.iou_loss_fwd_bwd_noalloc.restype = i32
     L.aug_num_variants.argtypes = [i32]
@@ -164,6 +167,18 @@ def iou_loss_fwd_bwd(d_descs: torch.Tensor, n_vols: int, p: torch.Tensor, n_clas
     _check(_L.iou_loss_fwd_bwd(_ptr(d_descs), int(n_vols), _ptr(p), int(n_classes),
                                _ptr(loss), _ptr(grad_p), _ptr(workspace), workspace.numel(),
                                _stream(stream)), "iou_loss_fwd_bwd")
+
+
+def seg_loss_fwd_bwd(d_descs: torch.Tensor, n_vols: int, x: torch.Tensor, n_classes: int,
+                     loss: torch.Tensor, grad_x: Optional[torch.Tensor],
+                     workspace: torch.Tensor, kind: int = AUG_LOSS_IOU, power: float = 1.0,
+                     logits: bool = False, stream=None):
+    """Overlap loss ``kind`` (IOU or Dice) of q = p^power, p = x or, with
+    ``logits``, the softmax of x over the classes; grad_x is with respect to x."""
+    _check(_L.seg_loss_fwd_bwd(_ptr(d_descs), int(n_vols), _ptr(x), int(n_classes), int(kind),
+                               float(power), int(bool(logits)), _ptr(loss), _ptr(grad_x),
+                               _ptr(workspace), workspace.numel(), _stream(stream)),
+           "seg_loss_fwd_bwd")
 
 
 def iou_loss_fwd_bwd_noalloc(d_descs: torch.Tensor, n_vols: int, p: torch.Tensor,
@@ -377,3 +392,29 @@ class IouLoss(torch.autograd.Function):
     @staticmethod
     def backward(ctx, grad):
         return ctx.gp * grad, None, None
+
+
+class SegLoss(torch.autograd.Function):
+    """Overlap loss of Sec. 5.C against nearest-warped labels, mean over classes
+    and batch: forward(x [B, C, onz, ony, onx], labels [B, D, H, W] uint8,
+    affine [B, 3, 4], kind, power, logits) -> scalar, with kind AUG_LOSS_IOU or
+    AUG_LOSS_DICE, p replaced by p^power, and x class scores (softmax fused)
+    when ``logits``; the gradient comes from the same fused call."""
+
+    @staticmethod
+    def forward(ctx, x, labels, affine, kind=AUG_LOSS_IOU, power=1.0, logits=False):
+        B, Cn = x.shape[0], x.shape[1]
+        onz, ony, onx = x.shape[2:]
+        x = x.contiguous()
+        batch = VolumeBatch([None] * B, affine, [(onx, ony, onz)] * B,
+                            labels=[labels[b] for b in range(B)], device=x.device)
+        ws = make_workspace(B, Cn, x.device)
+        loss = torch.empty(B, dtype=torch.float32, device=x.device)
+        gx = torch.empty_like(x) if ctx.needs_input_grad[0] else None
+        seg_loss_fwd_bwd(batch.d_descs, B, x, Cn, loss, gx, ws, kind, power, logits)
+        ctx.gx = gx
+        return loss.mean()
+
+    @staticmethod
+    def backward(ctx, grad):
+        return ctx.gx * grad, None, None, None, None, None

@@ -209,11 +209,12 @@ aug_status run_bwd(int variant, const aug_volume_desc* d, int n, const float* co
 }
 
 aug_status run_iou(int variant, const aug_volume_desc* d, int n, const float* p, int C,
-                   float* loss, float* gp, void* ws, cudaStream_t st) {
+                   float* loss, float* gp, void* ws, cudaStream_t st, int kind = AUG_LOSS_IOU,
+                   float power = 1.0f, bool logits = false) {
   double* partials = ws_partials(ws, n);
   float2* coefs = (float2*)((char*)partials + partial_bytes(n, C));
-  return from_cuda(launch_iou(variant, d, n, p, C, loss, gp, ws_table(ws), partials, coefs,
-                              (WsHeader*)ws, st));
+  return from_cuda(launch_iou(variant, d, n, p, C, kind, power, logits, loss, gp, ws_table(ws),
+                              partials, coefs, (WsHeader*)ws, st));
 }
 
 }  // namespace
@@ -282,6 +283,22 @@ aug_status iou_loss_fwd_bwd(const aug_volume_desc* d_descs, int n_vols, const fl
   if (s != AUG_OK) return s;
   return run_iou(variant_of(2), d_descs, n_vols, d_p, n_classes, d_loss, d_grad_p, d_workspace,
                  (cudaStream_t)stream);
+}
+
+aug_status seg_loss_fwd_bwd(const aug_volume_desc* d_descs, int n_vols, const float* d_x,
+                            int n_classes, int kind, float power, int logits, float* d_loss,
+                            float* d_grad_x, void* d_workspace, size_t workspace_bytes,
+                            aug_stream_t stream) {
+  if (n_vols < 1 || n_vols > kMaxVols || d_descs == nullptr || d_x == nullptr ||
+      d_loss == nullptr)
+    return AUG_ERR_INVALID_ARG;
+  if (kind != AUG_LOSS_IOU && kind != AUG_LOSS_DICE) return AUG_ERR_INVALID_ARG;
+  if (!(power > 0.0f) || !isfinite(power)) return AUG_ERR_INVALID_ARG;
+  if (n_classes < 1 || n_classes > kMaxClasses) return AUG_ERR_UNSUPPORTED;
+  const aug_status s = check_ws(d_workspace, workspace_bytes, n_vols, n_classes);
+  if (s != AUG_OK) return s;
+  return run_iou(variant_of(2), d_descs, n_vols, d_x, n_classes, d_loss, d_grad_x, d_workspace,
+                 (cudaStream_t)stream, kind, power, logits != 0);
 }
 
 int aug_num_variants(int op) { return n_variants(op); }

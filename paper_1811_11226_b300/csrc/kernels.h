@@ -36,9 +36,11 @@ cudaError_t launch_bwd(int variant, const aug_volume_desc* d, int n, const float
 
 int iou_num_variants();
 const char* iou_variant_name(int v);
+// Overlap loss `kind` (aug_loss_kind) on q = (logits ? softmax(p) : p)^power.
 cudaError_t launch_iou(int variant, const aug_volume_desc* d, int n, const float* p, int C,
-                       float* loss, float* gp, VolConst* tab, double* partials, float2* coefs,
-                       WsHeader* ws, cudaStream_t st);
+                       int kind, float power, bool logits, float* loss, float* gp,
+                       VolConst* tab, double* partials, float2* coefs, WsHeader* ws,
+                       cudaStream_t st);
 
 cudaError_t launch_philox(const uint32_t* ctr, long long n, unsigned k0, unsigned k1,
                           uint32_t* out, cudaStream_t st);

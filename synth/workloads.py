@@ -92,6 +92,16 @@ def softmax_probs(shape_cxyz_list, seed, device, logit_std=2.0, n_classes=N_CLAS
     return torch.cat(parts)
 
 
+def class_logits(shape_cxyz_list, seed, device, logit_std=2.0, n_classes=N_CLASSES):
+    """Packed class scores: per volume ``[C][onz][ony][onx]`` of
+    N(0, logit_std^2), volumes concatenated (the inputs of the fused softmax)."""
+    gen = _gen(device, seed)
+    parts = [torch.randn((n_classes, onz, ony, onx), generator=gen, device=torch.device(device),
+                         dtype=torch.float32).reshape(-1) * logit_std
+             for (onx, ony, onz) in shape_cxyz_list]
+    return torch.cat(parts)
+
+
 def upstream_grads(shape_list, seed, device):
     gen = _gen(device, seed)
     return [torch.randn((onz, ony, onx), generator=gen, device=torch.device(device),
