@@ -35,22 +35,28 @@ struct FwdP {
 
 // Final value of one output voxel: occluded voxels are exactly 0 (nothing
 // after the warp applies to them); otherwise the optional window clamp.
-template <typename TIn>
+// POST = false (a run that meets neither) compiles to nothing.
+template <bool POST, typename TIn>
 __device__ __forceinline__ float finish(const FwdP<TIn>& P, int k, float y) {
+  if (!POST) return y;
   if (k >= P.klo && k <= P.khi) return 0.0f;
   return P.window ? __saturatef(y) : y;
+}
+template <bool POST, typename TIn>
+__device__ __forceinline__ bool occluded(const FwdP<TIn>& P, int k) {
+  return POST && k >= P.klo && k <= P.khi;
 }
 
 // Exterior quad: every tap reads the fill value, so the sample is constant;
 // only the noise differs per voxel.  The coordinate advances by n steps at once.
-template <typename TIn, bool IMG, bool LAB>
+template <bool POST, typename TIn, bool IMG, bool LAB>
 __device__ __forceinline__ void fwd_quad_exterior(const FwdP<TIn>& P, int& o, int n, bool valid,
                                                   const float z[4], int kq) {
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
     if (m < n) {
       if (valid) {
-        if (IMG) __stcs(P.oimg + o, finish(P, kq + m, fmaf(P.sigma, z[m], P.yfill)));
+        if (IMG) __stcs(P.oimg + o, finish<POST>(P, kq + m, fmaf(P.sigma, z[m], P.yfill)));
         if (LAB) P.olab[o] = (uint8_t)P.fill_label;
       }
       o += P.plane;
@@ -64,7 +70,7 @@ __device__ __forceinline__ void fwd_quad_exterior(const FwdP<TIn>& P, int& o, in
 // samples is interpolated, and the quad's normals are computed while the
 // first group's loads are in flight.  PD trades registers (occupancy) for
 // memory-level parallelism; it is part of the kernel variant.
-template <typename TIn, int MODE, bool IMG, bool LAB, bool FULL, int PD>
+template <bool POST, typename TIn, int MODE, bool IMG, bool LAB, bool FULL, int PD>
 __device__ __forceinline__ void fwd_quad(const FwdP<TIn>& P, long long& sx, long long& sy,
                                          long long& sz, int& o, int n, bool valid,
                                          bool noisy, unsigned long long quad, unsigned noise_id,
@@ -86,7 +92,7 @@ __device__ __forceinline__ void fwd_quad(const FwdP<TIn>& P, long long& sx, long
         const int fx = q40_floor(sx), fy = q40_floor(sy), fz = q40_floor(sz);
         const int hbx = q40_halfbit(sx), hby = q40_halfbit(sy), hbz = q40_halfbit(sz);
         // An occluded voxel skips the image fetch (warp-uniform: one k per warp).
-        const bool fetch = !(kq + m >= P.klo && kq + m <= P.khi);
+        const bool fetch = !occluded<POST>(P, kq + m);
         if (IMG) {
           w[i][0] = q40_frac(sx);
           w[i][1] = q40_frac(sy);
@@ -162,8 +168,8 @@ __device__ __forceinline__ void fwd_quad(const FwdP<TIn>& P, long long& sx, long
                              fma2(pk2(P.a, P.a), v, pk2(P.b, P.b)));
         float y0, y1;
         upk2(y, y0, y1);
-        y0 = finish(P, kq + m, y0);
-        y1 = finish(P, kq + m + 1, y1);
+        y0 = finish<POST>(P, kq + m, y0);
+        y1 = finish<POST>(P, kq + m + 1, y1);
         if (valid) {
           __stcs(P.oimg + o, y0);
           if (LAB) P.olab[o] = (uint8_t)lab[i];
@@ -187,11 +193,51 @@ __device__ __forceinline__ void fwd_quad(const FwdP<TIn>& P, long long& sx, long
           const float c0 = fmaf(ty, c10 - c00, c00);
           const float c1 = fmaf(ty, c11 - c01, c01);
           const float v = fmaf(tz, c1 - c0, c0);
-          if (valid) __stcs(P.oimg + o, finish(P, kq + m, fmaf(P.sigma, z[m], fmaf(P.a, v, P.b))));
+          if (valid)
+            __stcs(P.oimg + o, finish<POST>(P, kq + m, fmaf(P.sigma, z[m], fmaf(P.a, v, P.b))));
         }
         if (LAB && valid) P.olab[o] = (uint8_t)lab[i];
         o += P.plane;
       }
+    }
+  }
+}
+
+// Quad-by-quad walk of a z-run: every quad is classified on its own (warp
+// vote), so a run that straddles the input boundary pays per-tap checks only
+// where needed.
+template <bool POST, typename TIn, int QZ, int PD, bool IMG, bool LAB>
+__device__ __forceinline__ void fwd_quads(const FwdP<TIn>& P, const TileCoord& tc, long long sx,
+                                          long long sy, long long sz, int o, bool noisy,
+                                          unsigned onx, unsigned ony, unsigned noise_id,
+                                          unsigned key0, unsigned key1) {
+  const long long ds[3] = {P.dx, P.dy, P.dz};
+#pragma unroll 1
+  for (int q = 0; q < QZ; ++q) {
+    const int kq = tc.k0 + 4 * q;
+    if (kq >= tc.k1) break;
+    const int n = min(4, tc.k1 - kq);
+    const unsigned long long quad =
+        ((unsigned long long)(kq >> 2) * ony + (unsigned)tc.jc) * onx + (unsigned)tc.ic;
+    const long long s[3] = {sx, sy, sz};
+    const int mode = warp_mode(classify_run<true>(s, ds, n - 1, P.nx, P.ny, P.nz));
+    if (mode == MODE_EXTERIOR) {
+      float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+      if (noisy) quad_normals(quad, noise_id, key0, key1, z);
+      fwd_quad_exterior<POST, TIn, IMG, LAB>(P, o, n, tc.valid, z, kq);
+      sx += (long long)n * P.dx;
+      sy += (long long)n * P.dy;
+      sz += (long long)n * P.dz;
+    } else if (n == 4) {
+      if (mode == MODE_INTERIOR)
+        fwd_quad<POST, TIn, MODE_INTERIOR, IMG, LAB, true, PD>(
+            P, sx, sy, sz, o, 4, tc.valid, noisy, quad, noise_id, key0, key1, kq);
+      else
+        fwd_quad<POST, TIn, MODE_GENERAL, IMG, LAB, true, PD>(
+            P, sx, sy, sz, o, 4, tc.valid, noisy, quad, noise_id, key0, key1, kq);
+    } else {
+      fwd_quad<POST, TIn, MODE_GENERAL, IMG, LAB, false, PD>(
+          P, sx, sy, sz, o, n, tc.valid, noisy, quad, noise_id, key0, key1, kq);
     }
   }
 }
@@ -229,62 +275,46 @@ __device__ __forceinline__ void fwd_tile_t(const VolConst& vc, int t, unsigned k
   long long sy = coord_q40(vc.tq[1], tc.ic, tc.jc, tc.k0);
   long long sz = coord_q40(vc.tq[2], tc.ic, tc.jc, tc.k0);
   const long long ds[3] = {P.dx, P.dy, P.dz};
-  int o = (tc.k0 * vc.ony + tc.jc) * vc.onx + tc.ic;
-  // One warp vote for the whole z-run; quads are re-classified only when the
-  // run straddles the input boundary.
-  const long long s0[3] = {sx, sy, sz};
-  const int run_mode = warp_mode(classify_run<true>(s0, ds, tc.k1 - 1 - tc.k0, P.nx, P.ny, P.nz));
-  const bool full_run = tc.k1 - tc.k0 == 4 * QZ;
-  if (run_mode == MODE_EXTERIOR) {
+  const int o = (tc.k0 * vc.ony + tc.jc) * vc.onx + tc.ic;
+  // Occlusion and window are decided per run (the z-range is the same for the
+  // whole CTA): runs that meet neither take the code without them.
+  const bool post = P.window || (P.klo <= P.khi && P.klo < tc.k1 && P.khi >= tc.k0);
+  if (!post) {
+    // One warp vote for the whole z-run; quads are re-classified only when
+    // the run straddles the input boundary.
+    const long long s0[3] = {sx, sy, sz};
+    const int run_mode =
+        warp_mode(classify_run<true>(s0, ds, tc.k1 - 1 - tc.k0, P.nx, P.ny, P.nz));
+    const bool full_run = tc.k1 - tc.k0 == 4 * QZ;
+    int oo = o;
+    if (run_mode == MODE_EXTERIOR) {
 #pragma unroll 1
-    for (int kq = tc.k0; kq < tc.k1; kq += 4) {
-      const int n = min(4, tc.k1 - kq);
-      float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-      if (noisy)
-        quad_normals(((unsigned long long)(kq >> 2) * ony + (unsigned)tc.jc) * onx +
-                         (unsigned)tc.ic,
-                     noise_id, key0, key1, z);
-      fwd_quad_exterior<TIn, IMG, LAB>(P, o, n, tc.valid, z, kq);
+      for (int kq = tc.k0; kq < tc.k1; kq += 4) {
+        const int n = min(4, tc.k1 - kq);
+        float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+        if (noisy)
+          quad_normals(((unsigned long long)(kq >> 2) * ony + (unsigned)tc.jc) * onx +
+                           (unsigned)tc.ic,
+                       noise_id, key0, key1, z);
+        fwd_quad_exterior<false, TIn, IMG, LAB>(P, oo, n, tc.valid, z, kq);
+      }
+      return;
     }
-    return;
-  }
-  if (run_mode == MODE_INTERIOR && full_run) {
+    if (run_mode == MODE_INTERIOR && full_run) {
 #pragma unroll 1
-    for (int kq = tc.k0; kq < tc.k1; kq += 4) {
-      const unsigned long long quad =
-          ((unsigned long long)(kq >> 2) * ony + (unsigned)tc.jc) * onx + (unsigned)tc.ic;
-      fwd_quad<TIn, MODE_INTERIOR, IMG, LAB, true, PD>(P, sx, sy, sz, o, 4, tc.valid, noisy, quad,
-                                                       noise_id, key0, key1, kq);
+      for (int kq = tc.k0; kq < tc.k1; kq += 4) {
+        const unsigned long long quad =
+            ((unsigned long long)(kq >> 2) * ony + (unsigned)tc.jc) * onx + (unsigned)tc.ic;
+        fwd_quad<false, TIn, MODE_INTERIOR, IMG, LAB, true, PD>(
+            P, sx, sy, sz, oo, 4, tc.valid, noisy, quad, noise_id, key0, key1, kq);
+      }
+      return;
     }
-    return;
-  }
-#pragma unroll 1
-  for (int q = 0; q < QZ; ++q) {
-    const int kq = tc.k0 + 4 * q;
-    if (kq >= tc.k1) break;
-    const int n = min(4, tc.k1 - kq);
-    const unsigned long long quad =
-        ((unsigned long long)(kq >> 2) * ony + (unsigned)tc.jc) * onx + (unsigned)tc.ic;
-    const long long s[3] = {sx, sy, sz};
-    const int mode = warp_mode(classify_run<true>(s, ds, n - 1, P.nx, P.ny, P.nz));
-    if (mode == MODE_EXTERIOR) {
-      float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-      if (noisy) quad_normals(quad, noise_id, key0, key1, z);
-      fwd_quad_exterior<TIn, IMG, LAB>(P, o, n, tc.valid, z, kq);
-      sx += (long long)n * P.dx;
-      sy += (long long)n * P.dy;
-      sz += (long long)n * P.dz;
-    } else if (n == 4) {
-      if (mode == MODE_INTERIOR)
-        fwd_quad<TIn, MODE_INTERIOR, IMG, LAB, true, PD>(P, sx, sy, sz, o, 4, tc.valid, noisy, quad,
-                                                     noise_id, key0, key1, kq);
-      else
-        fwd_quad<TIn, MODE_GENERAL, IMG, LAB, true, PD>(P, sx, sy, sz, o, 4, tc.valid, noisy, quad,
-                                                    noise_id, key0, key1, kq);
-    } else {
-      fwd_quad<TIn, MODE_GENERAL, IMG, LAB, false, PD>(P, sx, sy, sz, o, n, tc.valid, noisy, quad,
-                                                   noise_id, key0, key1, kq);
-    }
+    fwd_quads<false, TIn, QZ, PD, IMG, LAB>(P, tc, sx, sy, sz, o, noisy, onx, ony, noise_id,
+                                            key0, key1);
+  } else {
+    fwd_quads<true, TIn, QZ, PD, IMG, LAB>(P, tc, sx, sy, sz, o, noisy, onx, ony, noise_id, key0,
+                                           key1);
   }
 }
 
