@@ -82,9 +82,10 @@ def profile_traffic(name):
         return None
     kv = {}
     for line in open(p):
-        if ":" in line and line.strip().startswith(("dram_bytes_per_launch", "csrc_hash")):
+        line = line.strip().lstrip("-* ")
+        if ":" in line and line.startswith(("dram_bytes_per_launch", "csrc_hash")):
             k, v = line.split(":", 1)
-            kv[k.strip().lstrip("-* ")] = v.strip().strip("`")
+            kv[k.strip()] = v.strip().strip("`")
     if kv.get("csrc_hash") != kernel_source_hash() or "dram_bytes_per_launch" not in kv:
         return None
     return float(kv["dram_bytes_per_launch"])
