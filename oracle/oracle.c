@@ -475,3 +475,131 @@ ORACLE_EXPORT void oracle_loss(const float* x, const uint8_t* y, int n_classes, 
   free(p);
   free(g);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Random augmentation parameters of one volume (Sec. 4), drawn from        */
+/* Philox4x32-10 with key (lo32 seed, hi32 seed) and counter                 */
+/* (j, noise_id, lo32 draw, 0x80000000 | hi32 draw), j = 0..7: words        */
+/* w[4j..4j+3], uniforms u_n = (w_n >> 8) 2^-24 in [0, 1).  (The set top    */
+/* bit of the last counter word keeps these counters apart from the noise's, */
+/* whose last word is 0.)                                                    */
+/*                                                                           */
+/* spec (float32, this order):                                               */
+/*   [0..2] rot_max  [3..5] scale_min  [6..8] scale_max  [9..11] reflect_prob */
+/*   [12] shear_max  [13] generic_max  [14..16] extra_scale  [17..19] shift_max */
+/*   [20,21] photo_a range  [22,23] photo_b range  [24,25] sigma range       */
+/*   [26,27] window lo range  [28,29] window hi range  [30] occ_max_frac     */
+/* draw_mask: 1 affine, 2 intensity affine + sigma, 4 window (+ sigma),     */
+/*            8 occlusion.                                                   */
+/*                                                                           */
+/* Affine: angles g_r = rot_max_r (2u_r - 1) (u0..u2), scales               */
+/* s_r = min_r + (max_r - min_r) u_{3+r}, reflection sign -1 where          */
+/* u_{6+r} < reflect_prob_r, shear entries (0,1), (0,2), (1,2) =            */
+/* shear_max (2u - 1) (u9..u11), generic perturbation G (row-major) =        */
+/* generic_max (2u - 1) (u12..u20), displacement d_r = shift_max_r (2u - 1) */
+/* (u21..u23);                                                               */
+/*   A = (I + G) Rz(g_z) Ry(g_y) Rx(g_x) Sh diag(refl s) diag(extra),        */
+/*   b = c_in + d - A c_out,  c = (N - 1) / 2,                               */
+/* so that A c_out + b = c_in + d: the output centre lands on the input      */
+/* centre displaced by d.  T = (A | b) rounded to float32.                   */
+/* Intensity: a, b, sigma from their ranges (u24, u25, u26).  Window:        */
+/* lo, hi from their ranges (u27, u28), a = 1/(hi - lo), b = -lo/(hi - lo),  */
+/* sigma = (sigma range draw u26) / (hi - lo), flag 1.  Occlusion:           */
+/* dmax = occ_max_frac out_nz, dz = dmax u29, z0 = -dmax + (out_nz - 1 +     */
+/* dmax) u30, flag 2.  Groups that are not drawn leave their outputs as      */
+/* passed in.                                                                */
+/* ------------------------------------------------------------------------ */
+static void mat3_mul(const double a[9], const double b[9], double out[9]) {
+  double t[9];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double s = 0.0;
+      for (int k = 0; k < 3; ++k) s += a[3 * i + k] * b[3 * k + j];
+      t[3 * i + j] = s;
+    }
+  memcpy(out, t, sizeof(t));
+}
+
+static void rotation(int axis, double g, double m[9]) {
+  /* Rotation by angle g about coordinate axis `axis` (0 = x, 1 = y, 2 = z). */
+  const int pa[3] = {1, 0, 0}, pb[3] = {2, 2, 1};
+  const int a = pa[axis], b = pb[axis];
+  for (int i = 0; i < 9; ++i) m[i] = (i % 4 == 0) ? 1.0 : 0.0;
+  m[3 * a + a] = cos(g);
+  m[3 * a + b] = -sin(g);
+  m[3 * b + a] = sin(g);
+  m[3 * b + b] = cos(g);
+}
+
+ORACLE_EXPORT void oracle_sample_params(const float* spec, uint32_t draw_mask, uint64_t seed,
+                                        uint64_t draw, uint32_t noise_id,
+                                        const int64_t in_dims[3], const int64_t out_dims[3],
+                                        float T[12], float photo[3], int32_t* flags,
+                                        float occ[2], double d_out[3], double A_out[9]) {
+  const double two_m24 = 1.0 / 16777216.0;
+  uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+  double u[32];
+  for (uint32_t j = 0; j < 8; ++j) {
+    uint32_t ctr[4] = {j, noise_id, (uint32_t)draw, 0x80000000u | (uint32_t)(draw >> 32)};
+    uint32_t w[4];
+    oracle_philox4x32_10(ctr, key, w);
+    for (int n = 0; n < 4; ++n) u[4 * j + n] = (double)(w[n] >> 8) * two_m24;
+  }
+  double S[32];
+  for (int i = 0; i < 31; ++i) S[i] = (double)spec[i];
+
+  if (draw_mask & 1u) {
+    double g[3], s[3], refl[3], d[3];
+    for (int r = 0; r < 3; ++r) {
+      g[r] = S[r] * (2.0 * u[r] - 1.0);
+      s[r] = S[3 + r] + (S[6 + r] - S[3 + r]) * u[3 + r];
+      refl[r] = (u[6 + r] < S[9 + r]) ? -1.0 : 1.0;
+      d[r] = S[17 + r] * (2.0 * u[21 + r] - 1.0);
+    }
+    double IG[9], Rx[9], Ry[9], Rz[9], Sh[9], D[9], A[9];
+    for (int i = 0; i < 9; ++i) IG[i] = ((i % 4 == 0) ? 1.0 : 0.0) + S[13] * (2.0 * u[12 + i] - 1.0);
+    rotation(0, g[0], Rx);
+    rotation(1, g[1], Ry);
+    rotation(2, g[2], Rz);
+    for (int i = 0; i < 9; ++i) Sh[i] = (i % 4 == 0) ? 1.0 : 0.0;
+    Sh[1] = S[12] * (2.0 * u[9] - 1.0);
+    Sh[2] = S[12] * (2.0 * u[10] - 1.0);
+    Sh[5] = S[12] * (2.0 * u[11] - 1.0);
+    for (int i = 0; i < 9; ++i) D[i] = 0.0;
+    for (int r = 0; r < 3; ++r) D[4 * r] = refl[r] * s[r] * S[14 + r];
+    mat3_mul(IG, Rz, A);
+    mat3_mul(A, Ry, A);
+    mat3_mul(A, Rx, A);
+    mat3_mul(A, Sh, A);
+    mat3_mul(A, D, A);
+    for (int r = 0; r < 3; ++r) {
+      const double c_in = ((double)in_dims[r] - 1.0) / 2.0;
+      double Ac = 0.0;
+      for (int k = 0; k < 3; ++k) Ac += A[3 * r + k] * (((double)out_dims[k] - 1.0) / 2.0);
+      const double b = c_in + d[r] - Ac;
+      for (int k = 0; k < 3; ++k) T[4 * r + k] = (float)A[3 * r + k];
+      T[4 * r + 3] = (float)b;
+    }
+    if (d_out) memcpy(d_out, d, sizeof(d));
+    if (A_out) memcpy(A_out, A, sizeof(A));
+  }
+  const double sigma = S[24] + (S[25] - S[24]) * u[26];
+  if (draw_mask & 4u) {
+    const double lo = S[26] + (S[27] - S[26]) * u[27];
+    const double hi = S[28] + (S[29] - S[28]) * u[28];
+    photo[0] = (float)(1.0 / (hi - lo));
+    photo[1] = (float)(-lo / (hi - lo));
+    photo[2] = (float)(sigma / (hi - lo));
+    *flags |= 1;
+  } else if (draw_mask & 2u) {
+    photo[0] = (float)(S[20] + (S[21] - S[20]) * u[24]);
+    photo[1] = (float)(S[22] + (S[23] - S[22]) * u[25]);
+    photo[2] = (float)sigma;
+  }
+  if (draw_mask & 8u) {
+    const double dmax = S[30] * (double)out_dims[2];
+    occ[1] = (float)(dmax * u[29]);
+    occ[0] = (float)(-dmax + ((double)out_dims[2] - 1.0 + dmax) * u[30]);
+    *flags |= 2;
+  }
+}

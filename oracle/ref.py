@@ -39,6 +39,8 @@ def lib():
             L.oracle_warp_bwd.argtypes = [_vp, _int, _i64, _i64, _i64, _i64, _i64, _i64, _vp,
                                           _f32, _f32, _int, _f32, _f32, _vp, _vp, _vp, _vp]
             L.oracle_iou.argtypes = [_vp, _vp, _int, _i64, C.c_double, _vp, _vp, _vp]
+            L.oracle_sample_params.argtypes = [_vp, C.c_uint32, _u64, _u64, C.c_uint32, _vp,
+                                               _vp, _vp, _vp, _vp, _vp, _vp, _vp]
             L.oracle_loss.argtypes = [_vp, _vp, _int, _i64, _int, C.c_double, _int,
                                       C.c_double, _vp, _vp, _vp]
             _lib = L
@@ -223,3 +225,41 @@ def warp_loss(vols, x_packed, n_classes: int, kind: int = LOSS_IOU, m: float = 1
         off += n_classes * nvox
     return (np.asarray(losses), (np.concatenate(grads) if want_grad else None),
             np.stack(sums))
+
+
+# Fields of a parameter-sampling spec, in the oracle's float order (Sec. 4).
+SPEC_FIELDS = (("rot_max", 3), ("scale_min", 3), ("scale_max", 3), ("reflect_prob", 3),
+               ("shear_max", 1), ("generic_max", 1), ("extra_scale", 3), ("shift_max", 3),
+               ("photo_a", 2), ("photo_b", 2), ("sigma", 2), ("window_lo", 2),
+               ("window_hi", 2), ("occ_max_frac", 1))
+DRAW_AFFINE, DRAW_PHOTO, DRAW_WINDOW, DRAW_OCCLUDE = 1, 2, 4, 8
+
+
+def spec_floats(spec: dict) -> np.ndarray:
+    out = []
+    for name, n in SPEC_FIELDS:
+        v = np.atleast_1d(np.asarray(spec[name], np.float32))
+        assert v.size == n, name
+        out.extend(v.tolist())
+    return np.asarray(out, np.float32)
+
+
+def sample_params(spec: dict, draw_mask: int, seed: int, draw: int, noise_id: int, in_dims,
+                  out_dims, T=None, photo=(1.0, 0.0, 0.0), flags=0, occ=(0.0, 0.0)):
+    """Parameters of one volume drawn as in oracle_sample_params; fields that
+    are not drawn keep the values passed in.  Returns a dict with T [3, 4]
+    float32, photo_a, photo_b, sigma, flags, occ_z0, occ_dz (float32) and the
+    FP64 displacement d and matrix A (NaN where not drawn)."""
+    Tv = np.zeros(12, np.float32) if T is None else np.asarray(T, np.float32).reshape(12).copy()
+    ph = np.asarray(photo, np.float32).copy()
+    fl = np.asarray([flags], np.int32)
+    oc = np.asarray(occ, np.float32).copy()
+    d = np.full(3, np.nan)
+    A = np.full(9, np.nan)
+    sp = spec_floats(spec)
+    lib().oracle_sample_params(_ptr(sp), int(draw_mask), _u64(seed), _u64(draw), int(noise_id),
+                               _ptr(np.asarray(in_dims, np.int64)),
+                               _ptr(np.asarray(out_dims, np.int64)), _ptr(Tv), _ptr(ph), _ptr(fl),
+                               _ptr(oc), _ptr(d), _ptr(A))
+    return dict(T=Tv.reshape(3, 4), photo_a=ph[0], photo_b=ph[1], sigma=ph[2], flags=int(fl[0]),
+                occ_z0=oc[0], occ_dz=oc[1], d=d, A=A.reshape(3, 3))
