@@ -358,6 +358,32 @@ def run_ours(args, rank, world, local):
         log(f"[e2e] {ms_e2e:.3f} ms/step")
         del h_img, h_lab, h_oi, h_ol
 
+    if args.only == "all":
+        # ---- forward with the parameters drawn on the device (same ranges as the host
+        # draw of the batch: rotation +-15 deg, scale 0.9-1.1, shift +-10, a 0.9-1.1,
+        # b +-50, sigma 0-50), sampler + forward in one graph, new draw every replay ----
+        d_descs2 = batch.d_descs.clone()
+        spec = A.ParamSpec(rot_max=(np.deg2rad(15.0),) * 3, scale_min=(0.9,) * 3,
+                           scale_max=(1.1,) * 3, shift_max=(10.0,) * 3, photo_a=(0.9, 1.1),
+                           photo_b=(-50.0, 50.0), sigma=(0.0, 50.0),
+                           draw=A.AUG_DRAW_AFFINE | A.AUG_DRAW_PHOTO)
+        counter = torch.zeros(1, dtype=torch.int64, device=dev)
+
+        def sampled_step():
+            A.aug_sample_params(d_descs2, batch.n, spec, seed, counter=counter)
+            A.aug_warp_fwd(d_descs2, batch.n, seed, ws)
+        g2 = capture(sampled_step, stream)
+        ms_s = time_graph(g2, max(3, args.steps // 5), args.warmup, stream)
+        st, bad = A.aug_read_device_status(ws)
+        if st != 0:
+            raise RuntimeError(f"device status {A.status_string(st)} volume {bad}")
+        res["fwd_device_params"] = {
+            "value": round(world * n_out / (ms_s * 1e-3) / 1e9, 3), "unit": "Gvox/s",
+            "ms_per_step": round(ms_s, 4), "draws": int(counter.item()),
+            "workload": "same batch, affine + intensity drawn per volume on the device "
+                        "(aug_sample_params) inside the graph"}
+        log(f"[fwd+device params] {ms_s:.4f} ms/step")
+
     # ---- forward + backward, 8 x 128^3 --------------------------------------------------------
     if args.only in ("all", "fwd_bwd"):
         res["fwd_bwd"] = bench_fwd_bwd(args, A, D, dev, stream, seed, world)
@@ -630,6 +656,7 @@ def main():
                      "traffic": traffic, "alg_bytes_per_launch": res["alg"],
                      "kernel": "k_fwd_batched"},
         "fwd_bwd": res["fwd_bwd"],
+        "fwd_device_params": res.get("fwd_device_params"),
         "plain_fwd": res["plain"],
         "e2e": res["e2e"],
         "gpu_launches": res["launches"],

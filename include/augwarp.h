@@ -151,6 +151,67 @@ aug_status aug_warp_fwd(const aug_volume_desc* d_descs, int n_vols, uint64_t see
 aug_status aug_warp_fwd_volume(const aug_volume_desc* h_desc, uint64_t seed,
                                aug_stream_t stream);
 
+/* ---- device-side random parameters (Sec. 4) ----------------------------------
+ * Ranges of the per-volume random augmentation (all float32, host struct passed
+ * by value).  Angles in radians, lengths in voxels of the input grid.
+ *
+ * For volume v the sampler draws 32 uniforms u_0..u_31 in [0, 1) from
+ * Philox4x32-10 with key (lo32 seed, hi32 seed) and counters
+ * (j, noise_id_v, lo32 n, 0x80000000 | hi32 n), j = 0..7, as u = (w >> 8) 2^-24
+ * of the words w in order; n is the draw index (below).  The set top bit keeps
+ * these counters apart from the noise's (last word 0).  With x(u) = 2u - 1:
+ *   angles    g_r = rot_max_r x(u_r)                       r = 0, 1, 2 (x, y, z)
+ *   scales    s_r = scale_min_r + (scale_max_r - scale_min_r) u_{3+r}
+ *   reflect   refl_r = -1 if u_{6+r} < reflect_prob_r else +1
+ *   shear     Sh = I with Sh_01, Sh_02, Sh_12 = shear_max x(u_9), x(u_10), x(u_11)
+ *   generic   G_ij = generic_max x(u_{12+3i+j})
+ *   shift     d_r = shift_max_r x(u_{21+r})
+ *   A = (I + G) Rz(g_z) Ry(g_y) Rx(g_x) Sh diag(refl s) diag(extra_scale),
+ *   b = c_in + d - A c_out, c = (N - 1)/2 per axis  (Sec. 4: A c + b = c + d),
+ * computed in double and rounded to float32 into affine[].
+ *   intensity photo_a, photo_b, sigma from their [min, max] by u_24, u_25, u_26;
+ *   window    lo, hi from window_lo, window_hi by u_27, u_28; photo_a =
+ *             1/(hi - lo), photo_b = -lo/(hi - lo), noise_sigma = (sigma draw)
+ *             / (hi - lo), and flags |= AUG_FLAG_WINDOW;
+ *   occlusion dmax = occ_max_frac out_nz, occ_dz = dmax u_29,
+ *             occ_z0 = -dmax + (out_nz - 1 + dmax) u_30, flags |= AUG_FLAG_OCCLUDE.
+ * Rotation about x by g: rows (y, z) = (cos g, -sin g; sin g, cos g); about y:
+ * rows (x, z); about z: rows (x, y). */
+typedef struct {
+  float rot_max[3];
+  float scale_min[3], scale_max[3];
+  float reflect_prob[3];
+  float shear_max;
+  float generic_max;
+  float extra_scale[3];
+  float shift_max[3];
+  float photo_a[2], photo_b[2], sigma[2]; /* [min, max] */
+  float window_lo[2], window_hi[2];       /* [min, max]; window_lo[1] < window_hi[0] */
+  float occ_max_frac;                     /* in [0, 1] */
+  uint32_t draw;                          /* aug_draw bits */
+} aug_param_spec;
+
+typedef enum {
+  AUG_DRAW_AFFINE = 1,  /* affine[]                                              */
+  AUG_DRAW_PHOTO = 2,   /* photo_a, photo_b, noise_sigma (ignored with WINDOW)    */
+  AUG_DRAW_WINDOW = 4,  /* photo_a, photo_b, noise_sigma as a window; flags        */
+  AUG_DRAW_OCCLUDE = 8  /* occ_z0, occ_dz; flags                                   */
+} aug_draw;
+
+/* Draws the parameters of every volume into its descriptor (device memory):
+ * the fields of the groups in spec->draw are overwritten, the others kept.
+ * Reads in/out dims and noise_id.  The draw index is n = draw + *d_counter
+ * when d_counter (device uint64) is non-NULL, which the call then increments
+ * on the device, so a captured graph draws new parameters on every replay;
+ * with d_counter NULL, n = draw.  One small kernel on `stream`.
+ * AUG_ERR_INVALID_ARG: NULL descriptors, n_vols out of 1..65535, or a spec
+ * with a non-finite value, a negative range width or maximum, a probability
+ * or occ_max_frac outside [0, 1], scale_min <= 0, window_lo[1] >= window_hi[0],
+ * or unknown draw bits. */
+aug_status aug_sample_params(aug_volume_desc* d_descs, int n_vols, const aug_param_spec* spec,
+                             uint64_t seed, uint64_t draw, uint64_t* d_counter,
+                             aug_stream_t stream);
+
 /* ---- adjoint of the image warp ---------------------------------------------
  * For upstream gradients g_b (shape of out_image of volume b, float32):
  *   grad_in_b[n]    = sum_o photo_a g_b(o) w_{n}(o)       over in-volume taps,

@@ -27,6 +27,7 @@ AUG_F32, AUG_I16 = 0, 1
 AUG_FLAG_WINDOW, AUG_FLAG_OCCLUDE = 1, 2
 OP_FWD, OP_BWD, OP_IOU = 0, 1, 2
 AUG_LOSS_IOU, AUG_LOSS_DICE = 0, 1
+AUG_DRAW_AFFINE, AUG_DRAW_PHOTO, AUG_DRAW_WINDOW, AUG_DRAW_OCCLUDE = 1, 2, 4, 8
 
 # Layout of aug_volume_desc (144 bytes, 16-byte aligned).
 DESC_DTYPE = np.dtype({
@@ -69,6 +70,8 @@ def _load():
     L.iou_loss_fwd_bwd.restype = i32
     L.seg_loss_fwd_bwd.argtypes = [vp, i32, vp, i32, i32, C.c_float, i32, vp, vp, vp, sz, vp]
     L.seg_loss_fwd_bwd.restype = i32
+    L.aug_sample_params.argtypes = [vp, i32, vp, u64, u64, vp, vp]
+    L.aug_sample_params.restype = i32
     L.iou_loss_fwd_bwd_noalloc.argtypes = [vp, i32, vp, i32, vp, vp, vp, vp]
     L.iou_loss_fwd_bwd_noalloc.restype = i32
     L.aug_num_variants.argtypes = [i32]
@@ -179,6 +182,47 @@ def seg_loss_fwd_bwd(d_descs: torch.Tensor, n_vols: int, x: torch.Tensor, n_clas
                                float(power), int(bool(logits)), _ptr(loss), _ptr(grad_x),
                                _ptr(workspace), workspace.numel(), _stream(stream)),
            "seg_loss_fwd_bwd")
+
+
+class ParamSpec(C.Structure):
+    """Ranges of the device-side parameter draw (aug_param_spec): angles in
+    radians, lengths in input voxels, [min, max] pairs; ``draw`` is a mask of
+    AUG_DRAW_* bits."""
+    _fields_ = [("rot_max", C.c_float * 3), ("scale_min", C.c_float * 3),
+                ("scale_max", C.c_float * 3), ("reflect_prob", C.c_float * 3),
+                ("shear_max", C.c_float), ("generic_max", C.c_float),
+                ("extra_scale", C.c_float * 3), ("shift_max", C.c_float * 3),
+                ("photo_a", C.c_float * 2), ("photo_b", C.c_float * 2), ("sigma", C.c_float * 2),
+                ("window_lo", C.c_float * 2), ("window_hi", C.c_float * 2),
+                ("occ_max_frac", C.c_float), ("draw", C.c_uint32)]
+
+    def __init__(self, **kw):
+        base = dict(rot_max=(0.0, 0.0, 0.0), scale_min=(1.0, 1.0, 1.0),
+                    scale_max=(1.0, 1.0, 1.0), reflect_prob=(0.0, 0.0, 0.0), shear_max=0.0,
+                    generic_max=0.0, extra_scale=(1.0, 1.0, 1.0), shift_max=(0.0, 0.0, 0.0),
+                    photo_a=(1.0, 1.0), photo_b=(0.0, 0.0), sigma=(0.0, 0.0),
+                    window_lo=(-1000.0, -1000.0), window_hi=(1000.0, 1000.0),
+                    occ_max_frac=0.0, draw=AUG_DRAW_AFFINE)
+        base.update(kw)
+        super().__init__()
+        for name, _ in self._fields_:
+            v = base[name]
+            if isinstance(v, (tuple, list, np.ndarray)):
+                getattr(self, name)[:] = [float(x) for x in v]
+            else:
+                setattr(self, name, v)
+
+
+def aug_sample_params(d_descs: torch.Tensor, n_vols: int, spec: ParamSpec, seed: int,
+                      draw: int = 0, counter: Optional[torch.Tensor] = None, stream=None):
+    """Draws every volume's parameters into the device descriptors.  ``counter``:
+    optional int64 CUDA tensor of one element, added to ``draw`` and advanced
+    by the call (so graph replays draw new parameters)."""
+    if counter is not None:
+        assert counter.is_cuda and counter.dtype == torch.int64 and counter.numel() == 1
+    _check(_L.aug_sample_params(_ptr(d_descs), int(n_vols), C.byref(spec), _seed(seed),
+                                _seed(draw), _ptr(counter), _stream(stream)),
+           "aug_sample_params")
 
 
 def iou_loss_fwd_bwd_noalloc(d_descs: torch.Tensor, n_vols: int, p: torch.Tensor,
@@ -315,6 +359,12 @@ class VolumeBatch:
         """Re-copy the host descriptors to the device (e.g. after editing
         ``h_descs`` between CUDA-graph replays)."""
         self.d_descs.copy_(torch.from_numpy(self.h_descs.view(np.uint8).copy()))
+
+    def download(self):
+        """Refresh the host descriptors from the device (e.g. after
+        aug_sample_params wrote new parameters there)."""
+        self.h_descs = self.d_descs.cpu().numpy().view(DESC_DTYPE).copy()
+        return self.h_descs
 
     def out_voxels(self):
         return [int(self.h_descs["out_nx"][b]) * int(self.h_descs["out_ny"][b]) *

@@ -2,6 +2,7 @@
 // launch-shape selection (persistent grids sized from occupancy and the SM
 // count), kernel variants and the autotuner.
 #include <math.h>
+#include <stddef.h>
 #include <stdint.h>
 
 #include <map>
@@ -195,6 +196,28 @@ bool host_desc_ok(const aug_volume_desc& d) {
   return true;
 }
 
+// Checks of a parameter-sampling spec (see aug_sample_params).
+bool spec_ok(const aug_param_spec& p) {
+  const float* f = (const float*)&p;
+  for (size_t i = 0; i < offsetof(aug_param_spec, draw) / sizeof(float); ++i)
+    if (!isfinite(f[i])) return false;
+  auto range = [](const float* r) { return r[0] <= r[1]; };
+  for (int r = 0; r < 3; ++r) {
+    if (p.rot_max[r] < 0.0f || p.shift_max[r] < 0.0f) return false;
+    if (p.scale_min[r] <= 0.0f || p.scale_min[r] > p.scale_max[r]) return false;
+    if (!(p.reflect_prob[r] >= 0.0f && p.reflect_prob[r] <= 1.0f)) return false;
+  }
+  if (p.shear_max < 0.0f || p.generic_max < 0.0f) return false;
+  if (!range(p.photo_a) || !range(p.photo_b) || !range(p.sigma) || p.sigma[0] < 0.0f)
+    return false;
+  if (!range(p.window_lo) || !range(p.window_hi) || !(p.window_lo[1] < p.window_hi[0]))
+    return false;
+  if (!(p.occ_max_frac >= 0.0f && p.occ_max_frac <= 1.0f)) return false;
+  if (p.draw & ~(unsigned)(AUG_DRAW_AFFINE | AUG_DRAW_PHOTO | AUG_DRAW_WINDOW | AUG_DRAW_OCCLUDE))
+    return false;
+  return true;
+}
+
 aug_status run_fwd(int variant, const aug_volume_desc* d, int n, uint64_t seed, void* ws,
                    cudaStream_t st) {
   unsigned k0, k1;
@@ -299,6 +322,19 @@ aug_status seg_loss_fwd_bwd(const aug_volume_desc* d_descs, int n_vols, const fl
   if (s != AUG_OK) return s;
   return run_iou(variant_of(2), d_descs, n_vols, d_x, n_classes, d_loss, d_grad_x, d_workspace,
                  (cudaStream_t)stream, kind, power, logits != 0);
+}
+
+aug_status aug_sample_params(aug_volume_desc* d_descs, int n_vols, const aug_param_spec* spec,
+                             uint64_t seed, uint64_t draw, uint64_t* d_counter,
+                             aug_stream_t stream) {
+  if (d_descs == nullptr || spec == nullptr || n_vols < 1 || n_vols > kMaxVols)
+    return AUG_ERR_INVALID_ARG;
+  if (!spec_ok(*spec)) return AUG_ERR_INVALID_ARG;
+  unsigned k0, k1;
+  split_seed(seed, &k0, &k1);
+  return from_cuda(launch_sample_params(d_descs, n_vols, *spec, k0, k1, draw,
+                                        (unsigned long long*)d_counter,
+                                        (cudaStream_t)stream));
 }
 
 int aug_num_variants(int op) { return n_variants(op); }

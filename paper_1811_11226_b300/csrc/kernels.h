@@ -42,6 +42,11 @@ cudaError_t launch_iou(int variant, const aug_volume_desc* d, int n, const float
                        VolConst* tab, double* partials, float2* coefs, WsHeader* ws,
                        cudaStream_t st);
 
+// Per-volume random parameters into the descriptors (one CTA).
+cudaError_t launch_sample_params(aug_volume_desc* d, int n, const aug_param_spec& sp,
+                                 unsigned k0, unsigned k1, unsigned long long draw,
+                                 unsigned long long* counter, cudaStream_t st);
+
 cudaError_t launch_philox(const uint32_t* ctr, long long n, unsigned k0, unsigned k1,
                           uint32_t* out, cudaStream_t st);
 

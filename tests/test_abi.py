@@ -97,3 +97,10 @@ def test_host_argument_checks_without_gpu(aw):
     h["affine"][0, 0] = np.inf
     assert L.aug_warp_fwd_volume(h.ctypes.data_as(C.c_void_p), 0, None) == \
         aw.AUG_ERR_DESCRIPTOR
+
+
+def test_struct_sizes_match_the_header():
+    import ctypes
+    from paper_1811_11226_b300 import augwarp as A
+    assert A.DESC_DTYPE.itemsize == 144
+    assert ctypes.sizeof(A.ParamSpec) == 128
