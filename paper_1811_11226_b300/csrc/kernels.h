@@ -12,7 +12,6 @@ namespace augk {
 
 // Grid of a persistent launch: (resident CTAs per SM, capped at
 // kMaxCtasPerSm) * SM count of the current device.  Cached per kernel.
-constexpr int kMaxCtasPerSm = 16;
 int persistent_grid(const void* kernel, int block, size_t smem);
 int device_sm_count();
 

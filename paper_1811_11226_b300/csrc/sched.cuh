@@ -16,6 +16,10 @@
 
 namespace augk {
 
+// Cap on the resident CTAs per SM of a persistent launch (grid = min(resident,
+// cap) x SM count).
+constexpr int kMaxCtasPerSm = 16;
+
 template <int BLOCK>
 struct SchedSmem {
   int tile_pre[BLOCK + 1];        // exclusive prefix of tiles within the chunk
