@@ -603,3 +603,84 @@ ORACLE_EXPORT void oracle_sample_params(const float* spec, uint32_t draw_mask, u
     *flags |= 2;
   }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Anti-aliasing Gaussian of the resampling step (Sec. 5.A):                */
+/*   S(p) = sum_{a,b,c} g(a, b, c) E(p + (a, b, c)),                         */
+/*   g(x) = prod_k exp(-x_k^2 / sigma_k^2) / (normalisation over the support) */
+/* with E the input extended by `fill` outside the volume, the support       */
+/* |x_k| <= ceil(3 sigma_k) (a single tap where sigma_k = 0), and            */
+/* sigma_k = max(r / u_k - 1, 0) / 3 for spacing u_k and target resolution r */
+/* (both in mm; sigma in input voxels).  The triple sum is taken directly.   */
+/* ------------------------------------------------------------------------ */
+ORACLE_EXPORT double oracle_antialias_sigma(double r, double u) {
+  const double t = r / u - 1.0;
+  return (t > 0.0 ? t : 0.0) / 3.0;
+}
+
+ORACLE_EXPORT int oracle_gauss_radius(double sigma) {
+  return sigma > 0.0 ? (int)ceil(3.0 * sigma) : 0;
+}
+
+/* Normalised 1-D weights w[0..2R], w[R + a] for offset a. */
+ORACLE_EXPORT void oracle_gauss_weights(double sigma, double* w) {
+  const int R = oracle_gauss_radius(sigma);
+  double s = 0.0;
+  for (int a = -R; a <= R; ++a) {
+    w[R + a] = (R == 0) ? 1.0 : exp(-(double)a * (double)a / (sigma * sigma));
+    s += w[R + a];
+  }
+  for (int a = 0; a <= 2 * R; ++a) w[a] /= s;
+}
+
+static double smooth_at(const void* image, int is_i16, int64_t nx, int64_t ny, int64_t nz,
+                        const double* w[3], const int R[3], double fill, int64_t i, int64_t j,
+                        int64_t k) {
+  double s = 0.0;
+  for (int c = -R[2]; c <= R[2]; ++c)
+    for (int b = -R[1]; b <= R[1]; ++b)
+      for (int a = -R[0]; a <= R[0]; ++a) {
+        const int64_t x = i + a, y = j + b, z = k + c;
+        double v = fill;
+        if (x >= 0 && x < nx && y >= 0 && y < ny && z >= 0 && z < nz) {
+          const int64_t n = (z * ny + y) * nx + x;
+          v = is_i16 ? (double)((const int16_t*)image)[n] : (double)((const float*)image)[n];
+        }
+        s += w[0][R[0] + a] * w[1][R[1] + b] * w[2][R[2] + c] * v;
+      }
+  return s;
+}
+
+/* Smoothed value at output indices q (flattened (k*ny + j)*nx + i of the
+ * input grid), FP64. */
+ORACLE_EXPORT void oracle_smooth_points(const void* image, int is_i16, int64_t nx, int64_t ny,
+                                        int64_t nz, const double sigma[3], double fill,
+                                        const int64_t* q, int64_t n, double* out) {
+  double wx[64], wy[64], wz[64];
+  const double* w[3] = {wx, wy, wz};
+  int R[3];
+  for (int r = 0; r < 3; ++r) {
+    R[r] = oracle_gauss_radius(sigma[r]);
+    oracle_gauss_weights(sigma[r], (double*)w[r]);
+  }
+  for (int64_t m = 0; m < n; ++m) {
+    const int64_t i = q[m] % nx, j = (q[m] / nx) % ny, k = q[m] / (nx * ny);
+    out[m] = smooth_at(image, is_i16, nx, ny, nz, w, R, fill, i, j, k);
+  }
+}
+
+/* Whole smoothed volume, FP64. */
+ORACLE_EXPORT void oracle_smooth(const void* image, int is_i16, int64_t nx, int64_t ny,
+                                 int64_t nz, const double sigma[3], double fill, double* out) {
+  double wx[64], wy[64], wz[64];
+  const double* w[3] = {wx, wy, wz};
+  int R[3];
+  for (int r = 0; r < 3; ++r) {
+    R[r] = oracle_gauss_radius(sigma[r]);
+    oracle_gauss_weights(sigma[r], (double*)w[r]);
+  }
+  for (int64_t k = 0; k < nz; ++k)
+    for (int64_t j = 0; j < ny; ++j)
+      for (int64_t i = 0; i < nx; ++i)
+        out[(k * ny + j) * nx + i] = smooth_at(image, is_i16, nx, ny, nz, w, R, fill, i, j, k);
+}

@@ -41,6 +41,14 @@ def lib():
             L.oracle_iou.argtypes = [_vp, _vp, _int, _i64, C.c_double, _vp, _vp, _vp]
             L.oracle_sample_params.argtypes = [_vp, C.c_uint32, _u64, _u64, C.c_uint32, _vp,
                                                _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+            L.oracle_antialias_sigma.argtypes = [C.c_double, C.c_double]
+            L.oracle_antialias_sigma.restype = C.c_double
+            L.oracle_gauss_radius.argtypes = [C.c_double]
+            L.oracle_gauss_radius.restype = _int
+            L.oracle_gauss_weights.argtypes = [C.c_double, _vp]
+            L.oracle_smooth.argtypes = [_vp, _int, _i64, _i64, _i64, _vp, C.c_double, _vp]
+            L.oracle_smooth_points.argtypes = [_vp, _int, _i64, _i64, _i64, _vp, C.c_double, _vp,
+                                               _i64, _vp]
             L.oracle_loss.argtypes = [_vp, _vp, _int, _i64, _int, C.c_double, _int,
                                       C.c_double, _vp, _vp, _vp]
             _lib = L
@@ -263,3 +271,40 @@ def sample_params(spec: dict, draw_mask: int, seed: int, draw: int, noise_id: in
                                _ptr(oc), _ptr(d), _ptr(A))
     return dict(T=Tv.reshape(3, 4), photo_a=ph[0], photo_b=ph[1], sigma=ph[2], flags=int(fl[0]),
                 occ_z0=oc[0], occ_dz=oc[1], d=d, A=A.reshape(3, 3))
+
+
+def antialias_sigma(r: float, u: float) -> float:
+    """Smoothing factor of the 3 mm resampling (Sec. 5.A), in input voxels."""
+    return float(lib().oracle_antialias_sigma(float(r), float(u)))
+
+
+def gauss_radius(sigma: float) -> int:
+    return int(lib().oracle_gauss_radius(float(sigma)))
+
+
+def gauss_weights(sigma: float) -> np.ndarray:
+    R = gauss_radius(sigma)
+    w = np.empty(2 * R + 1, np.float64)
+    lib().oracle_gauss_weights(float(sigma), _ptr(w))
+    return w
+
+
+def smooth(image, sigma_xyz, fill: float) -> np.ndarray:
+    """Anti-aliasing Gaussian of a [nz, ny, nx] float32 / int16 volume (FP64 out)."""
+    img = _np(image)
+    nz, ny, nx = img.shape
+    out = np.empty(img.shape, np.float64)
+    lib().oracle_smooth(_ptr(img), int(img.dtype == np.int16), nx, ny, nz,
+                        _ptr(np.asarray(sigma_xyz, np.float64)), float(fill), _ptr(out))
+    return out
+
+
+def smooth_points(image, sigma_xyz, fill: float, q) -> np.ndarray:
+    img = _np(image)
+    nz, ny, nx = img.shape
+    q = np.ascontiguousarray(q, np.int64)
+    out = np.empty(q.shape, np.float64)
+    lib().oracle_smooth_points(_ptr(img), int(img.dtype == np.int16), nx, ny, nz,
+                               _ptr(np.asarray(sigma_xyz, np.float64)), float(fill), _ptr(q),
+                               q.size, _ptr(out))
+    return out
