@@ -393,6 +393,8 @@ def run_ours(args, rank, world, local):
         res["loss_variants"] = bench_loss_variants(args, A, dev, stream)
     if (args.only == "all" and args.all) or args.only == "train":
         res["train_step"] = bench_train(args, A, dev, stream, seed)
+    if (args.only == "all" and args.all) or args.only == "smooth":
+        res["antialias_smooth"] = bench_smooth(args, A, dev, stream)
     res["peak"], res["peak_kind"] = peak, peak_kind
     res["launches"] = args.steps  # one kernel per graph replay
     return res
@@ -525,6 +527,29 @@ def bench_train(args, A, dev, stream, seed):
             "workload": "16 int16 512^2 x 300-600 -> 128x128x160: fwd + IOU fwd/bwd + grad_T"}
 
 
+def bench_smooth(args, A, dev, stream):
+    """Anti-aliasing Gaussian of the 3 mm resampling (Sec. 5.A) on the 16
+    full-resolution int16 volumes (512^2 x 300-600, 0.7 mm -> 3 mm:
+    sigma = (3/0.7 - 1)/3 = 1.095 voxels, 9 taps per axis): int16 in, float32
+    out, HBM-bound at 6 bytes per voxel."""
+    from synth import workloads
+    w = workloads.config4(device=dev, n_vols=args.smooth_vols)
+    imgs = [v.image for v in w.vols]
+    outs = [torch.empty(im.shape, dtype=torch.float32, device=dev) for im in imgs]
+    s = A.aug_antialias_sigma(3.0, 0.7)
+    graph = capture(lambda: A.aug_smooth(imgs, outs, [(s, s, s)] * len(imgs)), stream)
+    ms = time_graph(graph, max(3, args.steps // 20), args.warmup, stream)
+    nvox = sum(im.numel() for im in imgs)
+    alg = nvox * (2 + 4)
+    peak, _ = hbm_peak()
+    log(f"[smooth] {ms:.4f} ms/step")
+    return {"value": round(nvox / (ms * 1e-3) / 1e9, 3), "unit": "Gvox/s (input voxels)",
+            "ms_per_step": round(ms, 4), "alg_GBps": round(alg / (ms * 1e-3) / 1e9, 1),
+            "frac_of_hbm": round(alg / (ms * 1e-3) / 1e9 / peak, 4),
+            "workload": f"{len(imgs)} int16 512^2 x 300-600 -> float32, sigma 1.095 "
+                        "(9 taps per axis)"}
+
+
 # ---- CPU baseline: the FP64 oracle ----------------------------------------------------------
 def cpu_baseline(min_seconds=15.0):
     from oracle import ref
@@ -601,11 +626,13 @@ def main():
     ap.add_argument("--all", action="store_true", help="also time the IOU and training-step "
                     "workloads")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--only", choices=["all", "fwd", "fwd_bwd", "iou", "loss", "train"],
+    ap.add_argument("--only", choices=["all", "fwd", "fwd_bwd", "iou", "loss", "train", "smooth"],
                     default="all", help="time one workload only (profiling runs)")
     ap.add_argument("--variant", type=int, default=-1,
                     help="fixed kernel variant instead of autotuning (profiling runs)")
     ap.add_argument("--no-preroll", action="store_true")
+    ap.add_argument("--smooth-vols", type=int, default=16,
+                    help="volumes of the smoothing workload (profiling runs use fewer)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
 
@@ -623,8 +650,8 @@ def main():
         return
     if args.only != "all":
         keep = {k: v for k, v in res.items() if k in ("fwd_bwd", "iou", "loss_variants",
-                                                       "train_step", "ms", "value", "variant",
-                                                       "achieved")}
+                                                       "train_step", "antialias_smooth", "ms",
+                                                       "value", "variant", "achieved")}
         print(json.dumps({"profile_run": args.only, **keep}), flush=True)
         return
     cpu = None
@@ -663,7 +690,7 @@ def main():
         "clocks": res["clocks"],
         "cpu_baseline": cpu,
     }
-    for key in ("iou", "loss_variants", "train_step"):
+    for key in ("iou", "loss_variants", "train_step", "antialias_smooth"):
         if key in res:
             line[key] = res[key]
     print(json.dumps(line), flush=True)

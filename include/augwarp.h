@@ -212,6 +212,43 @@ aug_status aug_sample_params(aug_volume_desc* d_descs, int n_vols, const aug_par
                              uint64_t seed, uint64_t draw, uint64_t* d_counter,
                              aug_stream_t stream);
 
+/* ---- anti-aliasing Gaussian of the 3 mm resampling (Sec. 5.A) ----------------
+ * out = the input smoothed by g(x) proportional to exp(-sum_k x_k^2 / sigma_k^2)
+ * on the support |x_k| <= ceil(3 sigma_k) (a single tap where sigma_k = 0),
+ * normalised to sum 1 per axis, with the input extended by `fill` outside its
+ * box (the same extension the warp uses).  Weights are computed in double and
+ * rounded to float32; the sums are float32.  A resampling to resolution r mm
+ * from spacing u_k mm uses sigma_k = aug_antialias_sigma(r, u_k), then the
+ * warp (aug_warp_fwd) with the downscaling affine reads `out`.
+ *
+ * h_descs: HOST array of n_vols descriptors (read during the call only).
+ * image: [nz][ny][nx] of image_dtype (device); out: [nz][ny][nx] float32
+ * (device, must not overlap image).  One launch per group of at most 32
+ * volumes with the same input type and radius, on `stream`.
+ * AUG_ERR_INVALID_ARG: NULL pointers, dims outside 1..8192 or >= 2^31
+ * voxels, unknown dtype, non-finite fill or sigma, sigma < 0.
+ * AUG_ERR_UNSUPPORTED: ceil(3 sigma_k) > 8 (sigma_k > 2.67). */
+typedef struct {
+  const void* image;
+  float* out;
+  int32_t nx, ny, nz;
+  int32_t image_dtype; /* aug_dtype */
+  float sigma[3];      /* x, y, z, in input voxels */
+  float fill;
+} aug_smooth_desc;
+
+aug_status aug_smooth(const aug_smooth_desc* h_descs, int n_vols, aug_stream_t stream);
+
+/* Device status of the smoothing calls since the last read: *status = 0;
+ * 1 if a block gave up waiting for its input tile, 2 if a block found its
+ * staging buffer misaligned (its outputs are then incomplete).  Synchronises
+ * the device, then clears the word. */
+aug_status aug_smooth_status(int* status);
+
+/* sigma = max(r / u - 1, 0) / 3: the smoothing factor of Sec. 5.A for target
+ * resolution r and spacing u (same unit), in input voxels.  Host function. */
+float aug_antialias_sigma(float r, float u);
+
 /* ---- adjoint of the image warp ---------------------------------------------
  * For upstream gradients g_b (shape of out_image of volume b, float32):
  *   grad_in_b[n]    = sum_o photo_a g_b(o) w_{n}(o)       over in-volume taps,

@@ -72,6 +72,12 @@ def _load():
     L.seg_loss_fwd_bwd.restype = i32
     L.aug_sample_params.argtypes = [vp, i32, vp, u64, u64, vp, vp]
     L.aug_sample_params.restype = i32
+    L.aug_smooth.argtypes = [vp, i32, vp]
+    L.aug_smooth.restype = i32
+    L.aug_smooth_status.argtypes = [vp]
+    L.aug_smooth_status.restype = i32
+    L.aug_antialias_sigma.argtypes = [C.c_float, C.c_float]
+    L.aug_antialias_sigma.restype = C.c_float
     L.iou_loss_fwd_bwd_noalloc.argtypes = [vp, i32, vp, i32, vp, vp, vp, vp]
     L.iou_loss_fwd_bwd_noalloc.restype = i32
     L.aug_num_variants.argtypes = [i32]
@@ -223,6 +229,43 @@ def aug_sample_params(d_descs: torch.Tensor, n_vols: int, spec: ParamSpec, seed:
     _check(_L.aug_sample_params(_ptr(d_descs), int(n_vols), C.byref(spec), _seed(seed),
                                 _seed(draw), _ptr(counter), _stream(stream)),
            "aug_sample_params")
+
+
+SMOOTH_DTYPE = np.dtype([("image", "<u8"), ("out", "<u8"), ("nx", "<i4"), ("ny", "<i4"),
+                         ("nz", "<i4"), ("image_dtype", "<i4"), ("sigma", "<f4", 3),
+                         ("fill", "<f4")])
+
+
+def aug_smooth_status() -> int:
+    """0, or 1 if a smoothing block gave up waiting for its input since the last
+    read (synchronises the device; clears the word)."""
+    st = C.c_int(0)
+    _check(_L.aug_smooth_status(C.byref(st)), "aug_smooth_status")
+    return st.value
+
+
+def aug_antialias_sigma(r: float, u: float) -> float:
+    """max(r/u - 1, 0)/3: Gaussian factor of the resampling of Sec. 5.A."""
+    return float(_L.aug_antialias_sigma(float(r), float(u)))
+
+
+def aug_smooth(images: Sequence[torch.Tensor], outs: Sequence[torch.Tensor], sigmas,
+               fill=-1000.0, stream=None):
+    """Anti-aliasing Gaussian of each [nz, ny, nx] float32/int16 CUDA volume into
+    the float32 volume of the same shape; ``sigmas``: per volume (sx, sy, sz)."""
+    n = len(images)
+    h = np.zeros(n, SMOOTH_DTYPE)
+    fl = np.broadcast_to(np.asarray(fill, np.float32), (n,))
+    for b, (img, out) in enumerate(zip(images, outs)):
+        assert img.is_cuda and img.is_contiguous() and img.dim() == 3
+        assert out.is_cuda and out.is_contiguous() and out.dtype == torch.float32
+        assert tuple(out.shape) == tuple(img.shape)
+        h["image"][b], h["out"][b] = img.data_ptr(), out.data_ptr()
+        h["nz"][b], h["ny"][b], h["nx"][b] = img.shape
+        h["image_dtype"][b] = _dtype_code(img)
+        h["sigma"][b] = np.asarray(sigmas[b], np.float32)
+        h["fill"][b] = fl[b]
+    _check(_L.aug_smooth(h.ctypes.data_as(C.c_void_p), n, _stream(stream)), "aug_smooth")
 
 
 def iou_loss_fwd_bwd_noalloc(d_descs: torch.Tensor, n_vols: int, p: torch.Tensor,

@@ -337,6 +337,45 @@ aug_status aug_sample_params(aug_volume_desc* d_descs, int n_vols, const aug_par
                                         (cudaStream_t)stream));
 }
 
+aug_status aug_smooth(const aug_smooth_desc* h_descs, int n_vols, aug_stream_t stream) {
+  if (h_descs == nullptr || n_vols < 1 || n_vols > kMaxVols) return AUG_ERR_INVALID_ARG;
+  for (int b = 0; b < n_vols; ++b) {
+    const aug_smooth_desc& d = h_descs[b];
+    auto dim_ok = [](int v) { return v >= 1 && v <= MAX_DIM; };
+    if (d.image == nullptr || d.out == nullptr) return AUG_ERR_INVALID_ARG;
+    if (!dim_ok(d.nx) || !dim_ok(d.ny) || !dim_ok(d.nz)) return AUG_ERR_INVALID_ARG;
+    const long long nvox = (long long)d.nx * d.ny * d.nz;
+    if (nvox >= (1LL << 31)) return AUG_ERR_INVALID_ARG;
+    if (d.image_dtype != AUG_F32 && d.image_dtype != AUG_I16) return AUG_ERR_INVALID_ARG;
+    if (!isfinite(d.fill)) return AUG_ERR_INVALID_ARG;
+    const char* i0 = (const char*)d.image;
+    const char* i1 = i0 + nvox * (d.image_dtype == AUG_I16 ? 2 : 4);
+    const char* o0 = (const char*)d.out;
+    if (o0 < i1 && i0 < o0 + nvox * 4) return AUG_ERR_INVALID_ARG;
+    for (int r = 0; r < 3; ++r) {
+      if (!isfinite(d.sigma[r]) || d.sigma[r] < 0.0f) return AUG_ERR_INVALID_ARG;
+      if (gauss_radius(d.sigma[r]) > smooth_max_radius()) return AUG_ERR_UNSUPPORTED;
+    }
+  }
+  return from_cuda(launch_smooth(h_descs, n_vols, (cudaStream_t)stream));
+}
+
+aug_status aug_smooth_status(int* status) {
+  if (status == nullptr) return AUG_ERR_INVALID_ARG;
+  int* word = nullptr;
+  if (smooth_status_word(&word) != cudaSuccess) return AUG_ERR_CUDA;
+  if (cudaDeviceSynchronize() != cudaSuccess) return AUG_ERR_CUDA;
+  if (cudaMemcpy(status, word, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    return AUG_ERR_CUDA;
+  if (cudaMemset(word, 0, sizeof(int)) != cudaSuccess) return AUG_ERR_CUDA;
+  return AUG_OK;
+}
+
+float aug_antialias_sigma(float r, float u) {
+  const double t = (double)r / (double)u - 1.0;
+  return (float)((t > 0.0 ? t : 0.0) / 3.0);
+}
+
 int aug_num_variants(int op) { return n_variants(op); }
 
 const char* aug_variant_name(int op, int variant) {

@@ -46,6 +46,12 @@ cudaError_t launch_sample_params(aug_volume_desc* d, int n, const aug_param_spec
                                  unsigned k0, unsigned k1, unsigned long long draw,
                                  unsigned long long* counter, cudaStream_t st);
 
+// Anti-aliasing Gaussian (host descriptors; grouped launches).
+int gauss_radius(float sigma);
+int smooth_max_radius();
+cudaError_t launch_smooth(const aug_smooth_desc* h, int n, cudaStream_t st);
+cudaError_t smooth_status_word(int** p);
+
 cudaError_t launch_philox(const uint32_t* ctr, long long n, unsigned k0, unsigned k1,
                           uint32_t* out, cudaStream_t st);
 
