@@ -249,6 +249,24 @@ aug_status aug_smooth_status(int* status);
  * resolution r and spacing u (same unit), in input voxels.  Host function. */
 float aug_antialias_sigma(float r, float u);
 
+/* ---- forward from host buffers, pipelined (Sec. 4, the host <-> device FIFO) --
+ * Same result as aug_warp_fwd on the same descriptors, for volumes that live
+ * in HOST memory: h_descs is a HOST array whose image, label, out_image and
+ * out_label point to host buffers (page-locked for the copies to overlap;
+ * pageable memory works but serialises).  The batch is processed in chunks of
+ * chunk_vols volumes on three internal streams and device slots: the input
+ * copy of one chunk, the kernel of the next and the output copy of the
+ * previous run at the same time.  The call is ordered after prior work on
+ * `stream`, and `stream` waits for all of it; the output buffers are valid
+ * once `stream` reaches that point.  Device memory: three slots sized for the
+ * largest chunk, from the stream-ordered pool (cudaMallocAsync), returned at
+ * the end of the call.  Calls on one device are serialised by the library.
+ * Errors: NULL h_descs, n_vols outside 1..65535 or chunk_vols < 1:
+ * AUG_ERR_INVALID_ARG; a descriptor failing the checks of
+ * aug_warp_fwd_volume: AUG_ERR_DESCRIPTOR (nothing is launched). */
+aug_status aug_warp_fwd_host(const aug_volume_desc* h_descs, int n_vols, uint64_t seed,
+                             int chunk_vols, aug_stream_t stream);
+
 /* ---- adjoint of the image warp ---------------------------------------------
  * For upstream gradients g_b (shape of out_image of volume b, float32):
  *   grad_in_b[n]    = sum_o photo_a g_b(o) w_{n}(o)       over in-volume taps,

@@ -72,6 +72,8 @@ def _load():
     L.seg_loss_fwd_bwd.restype = i32
     L.aug_sample_params.argtypes = [vp, i32, vp, u64, u64, vp, vp]
     L.aug_sample_params.restype = i32
+    L.aug_warp_fwd_host.argtypes = [vp, i32, u64, i32, vp]
+    L.aug_warp_fwd_host.restype = i32
     L.aug_smooth.argtypes = [vp, i32, vp]
     L.aug_smooth.restype = i32
     L.aug_smooth_status.argtypes = [vp]
@@ -160,6 +162,50 @@ def aug_warp_fwd_volume(h_desc: np.ndarray, seed: int, stream=None):
     h = np.ascontiguousarray(h_desc, dtype=DESC_DTYPE).reshape(1)
     _check(_L.aug_warp_fwd_volume(h.ctypes.data_as(C.c_void_p), _seed(seed), _stream(stream)),
            "aug_warp_fwd_volume")
+
+
+def aug_warp_fwd_host(h_descs: np.ndarray, seed: int, chunk_vols: int = 8, stream=None):
+    """Forward from HOST buffers (descriptor pointers are host addresses, ideally
+    page-locked), pipelined over chunks of volumes; ordered on ``stream``."""
+    h = np.ascontiguousarray(h_descs, dtype=DESC_DTYPE)
+    _check(_L.aug_warp_fwd_host(h.ctypes.data_as(C.c_void_p), len(h), _seed(seed),
+                                int(chunk_vols), _stream(stream)), "aug_warp_fwd_host")
+
+
+def host_descriptors(images, affines, out_shapes, labels=None, out_images=None, out_labels=None,
+                     photo_a=None, photo_b=None, noise_sigma=None, fill_image=-1000.0,
+                     fill_label=0, noise_ids=None):
+    """Descriptor array for aug_warp_fwd_host from CPU tensors (page-locked for
+    overlap): the same fields as VolumeBatch, with host addresses."""
+    B = len(out_shapes)
+    h = np.zeros(B, DESC_DTYPE)
+    h["affine"] = np.asarray(affines.detach().cpu() if torch.is_tensor(affines) else affines,
+                             np.float32).reshape(B, 12)
+    h["photo_a"] = 1.0 if photo_a is None else np.asarray(photo_a, np.float32)
+    h["photo_b"] = 0.0 if photo_b is None else np.asarray(photo_b, np.float32)
+    h["noise_sigma"] = 0.0 if noise_sigma is None else np.asarray(noise_sigma, np.float32)
+    h["fill_image"] = fill_image
+    h["fill_label"] = fill_label
+    h["noise_id"] = np.arange(B, dtype=np.uint32) if noise_ids is None else np.asarray(
+        noise_ids, np.uint32)
+    for b in range(B):
+        img = images[b]
+        assert not img.is_cuda and img.is_contiguous() and img.dim() == 3
+        h["image"][b] = img.data_ptr()
+        h["image_dtype"][b] = _dtype_code(img)
+        h["in_nz"][b], h["in_ny"][b], h["in_nx"][b] = img.shape
+        onx, ony, onz = (int(v) for v in out_shapes[b])
+        h["out_nx"][b], h["out_ny"][b], h["out_nz"][b] = onx, ony, onz
+        if labels is not None and labels[b] is not None:
+            assert not labels[b].is_cuda and labels[b].dtype == torch.uint8
+            h["label"][b] = labels[b].data_ptr()
+        if out_images is not None and out_images[b] is not None:
+            assert not out_images[b].is_cuda and tuple(out_images[b].shape) == (onz, ony, onx)
+            h["out_image"][b] = out_images[b].data_ptr()
+        if out_labels is not None and out_labels[b] is not None:
+            assert not out_labels[b].is_cuda and tuple(out_labels[b].shape) == (onz, ony, onx)
+            h["out_label"][b] = out_labels[b].data_ptr()
+    return h
 
 
 def aug_warp_bwd(d_descs: torch.Tensor, n_vols: int, d_grad_out_ptrs: torch.Tensor,

@@ -242,6 +242,16 @@ aug_status run_iou(int variant, const aug_volume_desc* d, int n, const float* p,
 
 }  // namespace
 
+namespace augk {
+cudaError_t fwd_on_device(const aug_volume_desc* d, int n, uint64_t seed, void* ws,
+                          cudaStream_t st) {
+  unsigned k0, k1;
+  split_seed(seed, &k0, &k1);
+  return launch_fwd_batched(variant_of(0), d, n, k0, k1, ws_table(ws), (WsHeader*)ws, st);
+}
+size_t fwd_workspace_bytes(int n_vols) { return ws_size(n_vols, 0); }
+}  // namespace augk
+
 extern "C" {
 
 size_t aug_workspace_size(int n_vols, int n_classes) { return ws_size(n_vols, n_classes); }
@@ -263,6 +273,16 @@ aug_status aug_read_device_status(void* d_workspace, aug_stream_t stream, int cl
   }
   if (bad_volume) *bad_volume = h[0] ? h[1] : -1;
   return (aug_status)h[0];
+}
+
+aug_status aug_warp_fwd_host(const aug_volume_desc* h_descs, int n_vols, uint64_t seed,
+                             int chunk_vols, aug_stream_t stream) {
+  if (h_descs == nullptr || n_vols < 1 || n_vols > kMaxVols || chunk_vols < 1)
+    return AUG_ERR_INVALID_ARG;
+  for (int b = 0; b < n_vols; ++b)
+    if (!host_desc_ok(h_descs[b])) return AUG_ERR_DESCRIPTOR;
+  return fwd_host_pipeline(h_descs, n_vols, seed, std::min(chunk_vols, n_vols),
+                           (cudaStream_t)stream);
 }
 
 aug_status aug_warp_fwd(const aug_volume_desc* d_descs, int n_vols, uint64_t seed,

@@ -52,6 +52,15 @@ int smooth_max_radius();
 cudaError_t launch_smooth(const aug_smooth_desc* h, int n, cudaStream_t st);
 cudaError_t smooth_status_word(int** p);
 
+// Batched forward on device descriptors with the default variant (the C ABI's
+// aug_warp_fwd without its argument checks), its workspace size, and the
+// pipelined forward from host buffers built on it.
+cudaError_t fwd_on_device(const aug_volume_desc* d, int n, uint64_t seed, void* ws,
+                          cudaStream_t st);
+size_t fwd_workspace_bytes(int n_vols);
+aug_status fwd_host_pipeline(const aug_volume_desc* h, int n, uint64_t seed, int chunk,
+                             cudaStream_t stream);
+
 cudaError_t launch_philox(const uint32_t* ctr, long long n, unsigned k0, unsigned k1,
                           uint32_t* out, cudaStream_t st);
 
