@@ -274,9 +274,13 @@ def run_ours(args, rank, world, local):
         if args.variant >= 0:
             A.aug_set_variant(A.OP_FWD, args.variant)
             best = args.variant
-        else:
+        elif args.autotune:
             with torch.cuda.stream(stream):
                 best, _ = A.aug_autotune(A.OP_FWD, batch, ws, seed=seed, reps=3)
+        else:
+            # The library's default variant: the kernel the DRAM-traffic record
+            # in profiles/ was captured on.
+            best = A.aug_get_variant(A.OP_FWD)
         variant = A.aug_variant_name(A.OP_FWD, best)
         graph = capture(lambda: A.aug_warp_fwd(batch.d_descs, batch.n, seed, ws), stream)
         # Pre-roll at load so the clock samples see the steady state.
@@ -682,7 +686,9 @@ def main():
     ap.add_argument("--only", choices=["all", "fwd", "fwd_bwd", "iou", "loss", "train", "smooth"],
                     default="all", help="time one workload only (profiling runs)")
     ap.add_argument("--variant", type=int, default=-1,
-                    help="fixed kernel variant instead of autotuning (profiling runs)")
+                    help="fixed forward kernel variant (default: the library's default)")
+    ap.add_argument("--autotune", action="store_true",
+                    help="pick the forward variant by timing all of them first")
     ap.add_argument("--no-preroll", action="store_true")
     ap.add_argument("--smooth-vols", type=int, default=16,
                     help="volumes of the smoothing workload (profiling runs use fewer)")
