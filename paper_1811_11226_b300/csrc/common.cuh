@@ -202,6 +202,37 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, unsigned k0, unsigned k1
   return c;
 }
 
+// The ten round keys of a Philox4x32-10 key, computed once (they depend only
+// on the seed, so a kernel computes them at entry, where they are uniform).
+struct PhiloxKey {
+  unsigned k0[10], k1[10];
+};
+__device__ __forceinline__ PhiloxKey philox_schedule(unsigned k0, unsigned k1) {
+  PhiloxKey k;
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    k.k0[r] = k0 + (unsigned)r * 0x9E3779B9u;
+    k.k1[r] = k1 + (unsigned)r * 0xBB67AE85u;
+  }
+  return k;
+}
+// The same rounds as philox4x32_10 with the scheduled keys.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const PhiloxKey& key) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+    const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+    c = make_uint4((unsigned)(p1 >> 32) ^ c.y ^ key.k0[r], (unsigned)p1,
+                   (unsigned)(p0 >> 32) ^ c.w ^ key.k1[r], (unsigned)p0);
+  }
+  return c;
+}
+
+// Streaming byte store to global memory.
+__device__ __forceinline__ void st_cs_u8(uint8_t* p, int v) {
+  asm volatile("st.global.cs.u8 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 // Documented approximate PTX instructions (special-function unit).
 __device__ __forceinline__ float lg2_approx(float x) {
   float r;
@@ -255,9 +286,9 @@ __device__ __forceinline__ float2 box_muller(unsigned ra, unsigned rb) {
 
 // Four normals of one quad (lanes 0..3).
 __device__ __forceinline__ void quad_normals(unsigned long long quad, unsigned noise_id,
-                                             unsigned k0, unsigned k1, float z[4]) {
+                                             const PhiloxKey& key, float z[4]) {
   const uint4 r = philox4x32_10(
-      make_uint4((unsigned)quad, (unsigned)(quad >> 32), noise_id, 0u), k0, k1);
+      make_uint4((unsigned)quad, (unsigned)(quad >> 32), noise_id, 0u), key);
   const float2 p = box_muller(r.x, r.y), q = box_muller(r.z, r.w);
   z[0] = p.x;
   z[1] = p.y;

@@ -57,7 +57,7 @@ __device__ __forceinline__ void fwd_quad_exterior(const FwdP<TIn>& P, int& o, in
     if (m < n) {
       if (valid) {
         if (IMG) __stcs(P.oimg + o, finish<POST>(P, kq + m, fmaf(P.sigma, z[m], P.yfill)));
-        if (LAB) P.olab[o] = (uint8_t)P.fill_label;
+        if (LAB) st_cs_u8(P.olab + o, P.fill_label);
       }
       o += P.plane;
     }
@@ -74,7 +74,7 @@ template <bool POST, typename TIn, int MODE, bool IMG, bool LAB, bool FULL, int 
 __device__ __forceinline__ void fwd_quad(const FwdP<TIn>& P, long long& sx, long long& sy,
                                          long long& sz, int& o, int n, bool valid,
                                          bool noisy, unsigned long long quad, unsigned noise_id,
-                                         unsigned key0, unsigned key1, int kq) {
+                                         const PhiloxKey& key, int kq) {
   float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
 #pragma unroll
   for (int g0 = 0; g0 < 4; g0 += PD) {
@@ -146,7 +146,7 @@ __device__ __forceinline__ void fwd_quad(const FwdP<TIn>& P, long long& sx, long
         sz += P.dz;
       }
     }
-    if (g0 == 0 && noisy) quad_normals(quad, noise_id, key0, key1, z);
+    if (g0 == 0 && noisy) quad_normals(quad, noise_id, key, z);
     if (FULL && IMG && PD >= 2) {
       // Voxel pairs share packed f32x2 instructions (same rounding as scalar).
 #pragma unroll
@@ -172,9 +172,9 @@ __device__ __forceinline__ void fwd_quad(const FwdP<TIn>& P, long long& sx, long
         y1 = finish<POST>(P, kq + m + 1, y1);
         if (valid) {
           __stcs(P.oimg + o, y0);
-          if (LAB) P.olab[o] = (uint8_t)lab[i];
+          if (LAB) st_cs_u8(P.olab + o, lab[i]);
           __stcs(P.oimg + o + P.plane, y1);
-          if (LAB) P.olab[o + P.plane] = (uint8_t)lab[i + 1];
+          if (LAB) st_cs_u8(P.olab + o + P.plane, lab[i + 1]);
         }
         o += 2 * P.plane;
       }
@@ -196,7 +196,7 @@ __device__ __forceinline__ void fwd_quad(const FwdP<TIn>& P, long long& sx, long
           if (valid)
             __stcs(P.oimg + o, finish<POST>(P, kq + m, fmaf(P.sigma, z[m], fmaf(P.a, v, P.b))));
         }
-        if (LAB && valid) P.olab[o] = (uint8_t)lab[i];
+        if (LAB && valid) st_cs_u8(P.olab + o, lab[i]);
         o += P.plane;
       }
     }
@@ -210,7 +210,7 @@ template <bool POST, typename TIn, int QZ, int PD, bool IMG, bool LAB>
 __device__ __forceinline__ void fwd_quads(const FwdP<TIn>& P, const TileCoord& tc, long long sx,
                                           long long sy, long long sz, int o, bool noisy,
                                           unsigned onx, unsigned ony, unsigned noise_id,
-                                          unsigned key0, unsigned key1) {
+                                          const PhiloxKey& key) {
   const long long ds[3] = {P.dx, P.dy, P.dz};
 #pragma unroll 1
   for (int q = 0; q < QZ; ++q) {
@@ -223,7 +223,7 @@ __device__ __forceinline__ void fwd_quads(const FwdP<TIn>& P, const TileCoord& t
     const int mode = warp_mode(classify_run<true>(s, ds, n - 1, P.nx, P.ny, P.nz));
     if (mode == MODE_EXTERIOR) {
       float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-      if (noisy) quad_normals(quad, noise_id, key0, key1, z);
+      if (noisy) quad_normals(quad, noise_id, key, z);
       fwd_quad_exterior<POST, TIn, IMG, LAB>(P, o, n, tc.valid, z, kq);
       sx += (long long)n * P.dx;
       sy += (long long)n * P.dy;
@@ -231,20 +231,19 @@ __device__ __forceinline__ void fwd_quads(const FwdP<TIn>& P, const TileCoord& t
     } else if (n == 4) {
       if (mode == MODE_INTERIOR)
         fwd_quad<POST, TIn, MODE_INTERIOR, IMG, LAB, true, PD>(
-            P, sx, sy, sz, o, 4, tc.valid, noisy, quad, noise_id, key0, key1, kq);
+            P, sx, sy, sz, o, 4, tc.valid, noisy, quad, noise_id, key, kq);
       else
         fwd_quad<POST, TIn, MODE_GENERAL, IMG, LAB, true, PD>(
-            P, sx, sy, sz, o, 4, tc.valid, noisy, quad, noise_id, key0, key1, kq);
+            P, sx, sy, sz, o, 4, tc.valid, noisy, quad, noise_id, key, kq);
     } else {
       fwd_quad<POST, TIn, MODE_GENERAL, IMG, LAB, false, PD>(
-          P, sx, sy, sz, o, n, tc.valid, noisy, quad, noise_id, key0, key1, kq);
+          P, sx, sy, sz, o, n, tc.valid, noisy, quad, noise_id, key, kq);
     }
   }
 }
 
 template <typename TIn, int NW, int QZ, int PD, bool IMG, bool LAB>
-__device__ __forceinline__ void fwd_tile_t(const VolConst& vc, int t, unsigned key0,
-                                           unsigned key1) {
+__device__ __forceinline__ void fwd_tile_t(const VolConst& vc, int t, const PhiloxKey& key) {
   const TileCoord tc = tile_coord<NW, QZ>(t, vc.onx, vc.ony, vc.onz);
   FwdP<TIn> P;
   P.img = (const TIn*)vc.image;
@@ -295,7 +294,7 @@ __device__ __forceinline__ void fwd_tile_t(const VolConst& vc, int t, unsigned k
         if (noisy)
           quad_normals(((unsigned long long)(kq >> 2) * ony + (unsigned)tc.jc) * onx +
                            (unsigned)tc.ic,
-                       noise_id, key0, key1, z);
+                       noise_id, key, z);
         fwd_quad_exterior<false, TIn, IMG, LAB>(P, oo, n, tc.valid, z, kq);
       }
       return;
@@ -306,36 +305,35 @@ __device__ __forceinline__ void fwd_tile_t(const VolConst& vc, int t, unsigned k
         const unsigned long long quad =
             ((unsigned long long)(kq >> 2) * ony + (unsigned)tc.jc) * onx + (unsigned)tc.ic;
         fwd_quad<false, TIn, MODE_INTERIOR, IMG, LAB, true, PD>(
-            P, sx, sy, sz, oo, 4, tc.valid, noisy, quad, noise_id, key0, key1, kq);
+            P, sx, sy, sz, oo, 4, tc.valid, noisy, quad, noise_id, key, kq);
       }
       return;
     }
     fwd_quads<false, TIn, QZ, PD, IMG, LAB>(P, tc, sx, sy, sz, o, noisy, onx, ony, noise_id,
-                                            key0, key1);
+                                            key);
   } else {
-    fwd_quads<true, TIn, QZ, PD, IMG, LAB>(P, tc, sx, sy, sz, o, noisy, onx, ony, noise_id, key0,
-                                           key1);
+    fwd_quads<true, TIn, QZ, PD, IMG, LAB>(P, tc, sx, sy, sz, o, noisy, onx, ony, noise_id,
+                                           key);
   }
 }
 
 template <int NW, int QZ, int PD>
-__device__ __forceinline__ void fwd_tile(const VolConst& vc, int t, unsigned key0,
-                                         unsigned key1) {
+__device__ __forceinline__ void fwd_tile(const VolConst& vc, int t, const PhiloxKey& key) {
   const bool img = vc.out_image != nullptr, lab = vc.out_label != nullptr;
   if (vc.dtype == AUG_I16) {
     if (img && lab)
-      fwd_tile_t<int16_t, NW, QZ, PD, true, true>(vc, t, key0, key1);
+      fwd_tile_t<int16_t, NW, QZ, PD, true, true>(vc, t, key);
     else if (img)
-      fwd_tile_t<int16_t, NW, QZ, PD, true, false>(vc, t, key0, key1);
+      fwd_tile_t<int16_t, NW, QZ, PD, true, false>(vc, t, key);
     else
-      fwd_tile_t<int16_t, NW, QZ, PD, false, true>(vc, t, key0, key1);
+      fwd_tile_t<int16_t, NW, QZ, PD, false, true>(vc, t, key);
   } else {
     if (img && lab)
-      fwd_tile_t<float, NW, QZ, PD, true, true>(vc, t, key0, key1);
+      fwd_tile_t<float, NW, QZ, PD, true, true>(vc, t, key);
     else if (img)
-      fwd_tile_t<float, NW, QZ, PD, true, false>(vc, t, key0, key1);
+      fwd_tile_t<float, NW, QZ, PD, true, false>(vc, t, key);
     else
-      fwd_tile_t<float, NW, QZ, PD, false, true>(vc, t, key0, key1);
+      fwd_tile_t<float, NW, QZ, PD, false, true>(vc, t, key);
   }
 }
 
@@ -346,12 +344,13 @@ __global__ void __launch_bounds__(NW * 32, MB)
     k_fwd_batched(const aug_volume_desc* __restrict__ descs, int n_vols,
                   const VolConst* __restrict__ tab, unsigned key0, unsigned key1) {
   __shared__ SchedSmem<NW * 32> sm;
+  const PhiloxKey key = philox_schedule(key0, key1);
   for_each_tile<NW, QZ>(
       descs, n_vols, sm, [](int, int) {},
       [&](int v, int t, long long) {
         const VolConst& vc = tab[v];
         if (vc.ok && (vc.out_image != nullptr || vc.out_label != nullptr))
-          fwd_tile<NW, QZ, PD>(vc, t, key0, key1);
+          fwd_tile<NW, QZ, PD>(vc, t, key);
       });
 }
 
@@ -362,7 +361,7 @@ __global__ void __launch_bounds__(NW * 32, MB)
   if (threadIdx.x == 0) make_volconst(desc, desc_valid(desc, desc.out_image != nullptr, false), vc);
   __syncthreads();
   if (!vc.ok) return;
-  fwd_tile<NW, QZ, PD>(vc, blockIdx.x, key0, key1);
+  fwd_tile<NW, QZ, PD>(vc, blockIdx.x, philox_schedule(key0, key1));
 }
 
 // ---- host launchers ----------------------------------------------------------
