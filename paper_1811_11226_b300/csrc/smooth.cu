@@ -62,11 +62,13 @@ struct SmoothVol {
 // sigma, so that the weights sit at fixed parameter offsets (the FMAs read
 // them from the constant bank instead of registers).
 struct SmoothBatch {
-  SmoothVol v[kSmMaxVols];
-  int tile_start[kSmMaxVols + 1];  // exclusive prefix of CTA tiles
+  // First, so that it lies in the first 4 KB of the parameters, where
+  // instructions can read it directly.
+  float w[3][2 * kSmMaxR + 1];  // per axis, offset a at [kSmMaxR + a]; zero outside its radius
   int n;
   int* status;
-  float w[3][2 * kSmMaxR + 1];  // per axis, offset a at [kSmMaxR + a]; zero outside its radius
+  int tile_start[kSmMaxVols + 1];  // exclusive prefix of CTA tiles
+  SmoothVol v[kSmMaxVols];
 };
 
 __device__ int g_smooth_status;
@@ -276,11 +278,16 @@ __global__ void __launch_bounds__(256, R <= 4 ? 3 : 2)
 #pragma unroll
   for (int c = 0; c < K; ++c) ring0[c] = ring1[c] = pk2(0.0f, 0.0f);
 
-  // One input slice; U (compile time) is its ring slot, zi = zb + U.  Returns
-  // false when the CTA must stop (a copy never arrived).
+  // One input slice; U (compile time) is its ring slot, zi = zb + U.  OUT: the
+  // slice completes an output slice (every slice but the first 2R of the CTA);
+  // FULL: every output of the tile lies inside the volume.  Returns false when
+  // the CTA must stop (a copy never arrived).
   int zb = zs;
-  auto step = [&](auto slot) -> bool {
+  const bool full_tile = tx0 + kSmTX <= nx && ty0 + kSmTY <= ny;
+  auto step = [&](auto slot, auto out_c, auto full_c) -> bool {
     constexpr int U = decltype(slot)::value;
+    constexpr bool OUT = decltype(out_c)::value;
+    constexpr bool FULL = decltype(full_c)::value;
     const int zi = zb + U;
     if (zi >= ze) return true;
     const int b = (zi - zs) & 1;
@@ -365,7 +372,7 @@ __global__ void __launch_bounds__(256, R <= 4 ? 3 : 2)
     ring0[U] = y0;
     ring1[U] = y1;
     const int zo = zi - R;
-    if (zo >= z0 && ox < nx) {
+    if (OUT && (FULL || ox < nx)) {
       f32x2 o0 = pk2(0.0f, 0.0f), o1 = pk2(0.0f, 0.0f);
 #pragma unroll
       for (int c = 0; c < K; ++c) {
@@ -375,11 +382,11 @@ __global__ void __launch_bounds__(256, R <= 4 ? 3 : 2)
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int oy = ty0 + 2 * warp + h;
-        if (oy < ny) {
+        if (FULL || oy < ny) {
           float a, c;
           upk2(h == 0 ? o0 : o1, a, c);
           float* dst = V.out + ((size_t)zo * ny + oy) * (size_t)nx + ox;
-          if (pair_ok && vec_store) {
+          if ((FULL || pair_ok) && vec_store) {
             __stcs(reinterpret_cast<float2*>(dst), make_float2(a, c));
           } else {
             __stcs(dst, a);
@@ -390,9 +397,26 @@ __global__ void __launch_bounds__(256, R <= 4 ? 3 : 2)
     }
     return true;
   };
+  // The first round holds the CTA's first K input slices: only its last slot
+  // completes an output slice.  Later rounds complete one per slot.
+  auto run = [&](auto full_c) -> bool {
+    if (!for_each_slot(std::make_integer_sequence<int, K>{}, [&](auto slot) {
+          constexpr int U = decltype(slot)::value;
+          return step(slot, std::integral_constant<bool, U == K - 1>{}, full_c);
+        }))
+      return false;
 #pragma unroll 1
-  for (; zb < ze; zb += K)
-    if (!for_each_slot(std::make_integer_sequence<int, K>{}, step)) return;
+    for (zb += K; zb < ze; zb += K)
+      if (!for_each_slot(std::make_integer_sequence<int, K>{}, [&](auto slot) {
+            return step(slot, std::true_type{}, full_c);
+          }))
+        return false;
+    return true;
+  };
+  if (full_tile)
+    run(std::true_type{});
+  else
+    run(std::false_type{});
 }
 
 namespace {
