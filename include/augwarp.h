@@ -328,7 +328,8 @@ aug_status iou_loss_fwd_bwd(const aug_volume_desc* d_descs, int n_vols, const fl
  * Layouts as iou_loss_fwd_bwd (d_x, d_grad_x: [C][out_nz][out_ny][out_nx] per
  * volume, packed).  power must be finite and > 0 (else AUG_ERR_INVALID_ARG);
  * with power < 1 a probability of exactly 0 has an infinite derivative.
- * p^power, exp and the reciprocal use the hardware approximations (relative
+ * p^power is a product for power 2, 3 or 4 and the hardware log2/exp2
+ * otherwise; exp and the reciprocal use the hardware approximations (relative
  * error ~1e-6).  Variants and autotuning are shared with op 2. */
 typedef enum { AUG_LOSS_IOU = 0, AUG_LOSS_DICE = 1 } aug_loss_kind;
 

@@ -36,12 +36,23 @@ namespace augk {
 
 enum { XF_POW = 1, XF_LOGITS = 2 };
 
-// p^m for p >= 0, m > 0 (hardware log2/exp2; 0 at p = 0).
+// p^m for p >= 0, m > 0: products for m = 2, 3, 4 (the kernel argument m is
+// uniform, so the choice is a uniform branch), else hardware log2/exp2 (0 at
+// p = 0).
 __device__ __forceinline__ float pow_pos(float p, float m) {
+  if (m == 2.0f) return p * p;
+  if (m == 3.0f) return p * p * p;
+  if (m == 4.0f) {
+    const float q = p * p;
+    return q * q;
+  }
   return p > 0.0f ? ex2_approx(m * lg2_approx(p)) : 0.0f;
 }
 // d(p^m)/dp = m p^(m-1); at p = 0: 0 (m > 1), 1 (m = 1), +inf (m < 1).
 __device__ __forceinline__ float dpow_pos(float p, float m) {
+  if (m == 2.0f) return 2.0f * p;
+  if (m == 3.0f) return 3.0f * (p * p);
+  if (m == 4.0f) return 4.0f * (p * p * p);
   if (p > 0.0f) return m * ex2_approx((m - 1.0f) * lg2_approx(p));
   return m > 1.0f ? 0.0f : (m == 1.0f ? 1.0f : __int_as_float(0x7f800000));
 }

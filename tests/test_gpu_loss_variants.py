@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 
 # (kind, power, logits)
 VARIANTS = [(1, 1.0, False), (0, 2.0, False), (1, 0.5, False), (0, 1.0, True),
-            (1, 1.0, True), (0, 3.0, True), (1, 1.5, True)]
+            (1, 1.0, True), (0, 3.0, True), (1, 1.5, True), (1, 4.0, False)]
 
 
 def run_loss(cases, x, C, kind, power, logits, want_grad=True, variant=None):
