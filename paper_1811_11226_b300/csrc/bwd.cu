@@ -192,7 +192,7 @@ __device__ __forceinline__ void bwd_tile(const VolConst& vc, BwdShared<NW>& sh, 
 }
 
 template <int NW, int QZ, bool GIN, bool GT>
-__global__ void __launch_bounds__(NW * 32)
+__global__ void __launch_bounds__(NW * 32, 1024 / (NW * 32))
     k_bwd_batched(const aug_volume_desc* __restrict__ descs, int n_vols,
                   const VolConst* __restrict__ tab, const float* const* gout,
                   float* const* gin, double* partials) {
