@@ -73,22 +73,27 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profile_traffic(name):
-    """DRAM bytes per launch recorded in profiles/<name>.md by an ncu capture
-    ('dram_bytes_per_launch: N' and 'csrc_hash: H'); None if absent or if the
-    kernels changed since the capture."""
+def profile_record(name, key):
+    """A per-launch figure recorded in profiles/<name>.md from an ncu capture
+    ('<key>: N' beside 'csrc_hash: H'); None if absent or if the kernel's
+    sources changed since the capture."""
     p = os.path.join(ROOT, "profiles", f"{name}.md")
     if not os.path.exists(p):
         return None
     kv = {}
     for line in open(p):
         line = line.strip().lstrip("-* ")
-        if ":" in line and line.startswith(("dram_bytes_per_launch", "csrc_hash")):
+        if ":" in line and line.startswith((key, "csrc_hash")):
             k, v = line.split(":", 1)
             kv[k.strip()] = v.strip().strip("`")
-    if kv.get("csrc_hash") != kernel_source_hash() or "dram_bytes_per_launch" not in kv:
+    if kv.get("csrc_hash") != kernel_source_hash() or key not in kv:
         return None
-    return float(kv["dram_bytes_per_launch"])
+    return float(kv[key])
+
+
+def profile_traffic(name):
+    """DRAM bytes per launch of the recorded capture (see profile_record)."""
+    return profile_record(name, "dram_bytes_per_launch")
 
 
 class ClockSampler:
@@ -768,6 +773,10 @@ def main():
                      "frac_of_nominal_7700": round(res["achieved"] / 7700.0, 4),
                      "traffic": traffic, "alg_bytes_per_launch": res["alg"],
                      "kernel": "k_fwd_batched"},
+        # The forward is limited by instruction issue, not DRAM: its recorded
+        # warp instructions per launch over the measured launch time, against
+        # 4 schedulers x SMs x the SM clock sampled during the timed region.
+        "issue": issue_roofline(res),
         "fwd_bwd": res["fwd_bwd"],
         "fwd_device_params": res.get("fwd_device_params"),
         "plain_fwd": res["plain"],
@@ -780,6 +789,19 @@ def main():
         if key in res:
             line[key] = res[key]
     print(json.dumps(line), flush=True)
+
+
+def issue_roofline(res):
+    inst = profile_record("fwd_batched_config1", "warp_inst_per_launch")
+    sm_mhz = (res.get("clocks") or {}).get("sm_mhz")
+    if inst is None or not sm_mhz:
+        return None
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peak = 4.0 * sms * sm_mhz * 1e6 / 1e9      # G warp instructions / s
+    achieved = inst / (res["ms"] * 1e-3) / 1e9
+    return {"bound": "issue", "achieved": round(achieved, 1), "peak": round(peak, 1),
+            "unit": "G warp inst/s", "frac": round(achieved / peak, 4),
+            "warp_inst_per_launch": int(inst), "kernel": "k_fwd_batched"}
 
 
 def peak_kind_note(kind):
