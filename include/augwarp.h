@@ -249,6 +249,15 @@ aug_status aug_smooth_status(int* status);
  * resolution r and spacing u (same unit), in input voxels.  Host function. */
 float aug_antialias_sigma(float r, float u);
 
+/* Test of the smoothing kernel's bounded waits (no counterpart in the paper):
+ * runs aug_smooth on at most 4 descriptors without issuing any tile copy, so
+ * every block's wait for its first tile runs out (after about a second), is
+ * recorded as status 1 (read with aug_smooth_status) and the block returns.
+ * Outputs are left incomplete.  Volumes whose rows are not a multiple of 16
+ * bytes use per-thread loads and do not wait. */
+aug_status aug_test_smooth_wait_timeout(const aug_smooth_desc* h_descs, int n_vols,
+                                        aug_stream_t stream);
+
 /* ---- forward from host buffers, pipelined (Sec. 4, the host <-> device FIFO) --
  * Same result as aug_warp_fwd on the same descriptors, for volumes that live
  * in HOST memory: h_descs is a HOST array whose image, label, out_image and

@@ -76,6 +76,8 @@ def _load():
     L.aug_warp_fwd_host.restype = i32
     L.aug_smooth.argtypes = [vp, i32, vp]
     L.aug_smooth.restype = i32
+    L.aug_test_smooth_wait_timeout.argtypes = [vp, i32, vp]
+    L.aug_test_smooth_wait_timeout.restype = i32
     L.aug_smooth_status.argtypes = [vp]
     L.aug_smooth_status.restype = i32
     L.aug_antialias_sigma.argtypes = [C.c_float, C.c_float]
@@ -295,10 +297,7 @@ def aug_antialias_sigma(r: float, u: float) -> float:
     return float(_L.aug_antialias_sigma(float(r), float(u)))
 
 
-def aug_smooth(images: Sequence[torch.Tensor], outs: Sequence[torch.Tensor], sigmas,
-               fill=-1000.0, stream=None):
-    """Anti-aliasing Gaussian of each [nz, ny, nx] float32/int16 CUDA volume into
-    the float32 volume of the same shape; ``sigmas``: per volume (sx, sy, sz)."""
+def _smooth_descs(images, outs, sigmas, fill):
     n = len(images)
     h = np.zeros(n, SMOOTH_DTYPE)
     fl = np.broadcast_to(np.asarray(fill, np.float32), (n,))
@@ -311,7 +310,23 @@ def aug_smooth(images: Sequence[torch.Tensor], outs: Sequence[torch.Tensor], sig
         h["image_dtype"][b] = _dtype_code(img)
         h["sigma"][b] = np.asarray(sigmas[b], np.float32)
         h["fill"][b] = fl[b]
-    _check(_L.aug_smooth(h.ctypes.data_as(C.c_void_p), n, _stream(stream)), "aug_smooth")
+    return h
+
+
+def aug_test_smooth_wait_timeout(images, outs, sigmas, fill=-1000.0, stream=None):
+    """The smoothing kernel with no tile copies issued: every wait runs out and
+    is recorded in the smoothing status (a test of the bounded waits)."""
+    h = _smooth_descs(images, outs, sigmas, fill)
+    _check(_L.aug_test_smooth_wait_timeout(h.ctypes.data_as(C.c_void_p), len(h),
+                                           _stream(stream)), "aug_test_smooth_wait_timeout")
+
+
+def aug_smooth(images: Sequence[torch.Tensor], outs: Sequence[torch.Tensor], sigmas,
+               fill=-1000.0, stream=None):
+    """Anti-aliasing Gaussian of each [nz, ny, nx] float32/int16 CUDA volume into
+    the float32 volume of the same shape; ``sigmas``: per volume (sx, sy, sz)."""
+    h = _smooth_descs(images, outs, sigmas, fill)
+    _check(_L.aug_smooth(h.ctypes.data_as(C.c_void_p), len(h), _stream(stream)), "aug_smooth")
 
 
 def iou_loss_fwd_bwd_noalloc(d_descs: torch.Tensor, n_vols: int, p: torch.Tensor,

@@ -382,6 +382,12 @@ aug_status aug_smooth(const aug_smooth_desc* h_descs, int n_vols, aug_stream_t s
   return from_cuda(launch_smooth(h_descs, n_vols, (cudaStream_t)stream));
 }
 
+aug_status aug_test_smooth_wait_timeout(const aug_smooth_desc* h_descs, int n_vols,
+                                        aug_stream_t stream) {
+  if (h_descs == nullptr || n_vols < 1 || n_vols > 4) return AUG_ERR_INVALID_ARG;
+  return from_cuda(launch_smooth(h_descs, n_vols, (cudaStream_t)stream, true));
+}
+
 aug_status aug_smooth_status(int* status) {
   if (status == nullptr) return AUG_ERR_INVALID_ARG;
   int* word = nullptr;

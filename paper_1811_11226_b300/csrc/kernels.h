@@ -49,7 +49,9 @@ cudaError_t launch_sample_params(aug_volume_desc* d, int n, const aug_param_spec
 // Anti-aliasing Gaussian (host descriptors; grouped launches).
 int gauss_radius(float sigma);
 int smooth_max_radius();
-cudaError_t launch_smooth(const aug_smooth_desc* h, int n, cudaStream_t st);
+// no_copies: the test of the bounded waits (no tile copy is issued).
+cudaError_t launch_smooth(const aug_smooth_desc* h, int n, cudaStream_t st,
+                          bool no_copies = false);
 cudaError_t smooth_status_word(int** p);
 
 // Batched forward on device descriptors with the default variant (the C ABI's

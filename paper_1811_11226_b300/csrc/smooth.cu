@@ -66,6 +66,7 @@ struct SmoothBatch {
   // instructions can read it directly.
   float w[3][2 * kSmMaxR + 1];  // per axis, offset a at [kSmMaxR + a]; zero outside its radius
   int n;
+  int no_copies;  // test of the bounded waits: issue no tile copy, so every wait runs out
   int* status;
   int tile_start[kSmMaxVols + 1];  // exclusive prefix of CTA tiles
   SmoothVol v[kSmMaxVols];
@@ -265,7 +266,7 @@ __global__ void __launch_bounds__(256, R <= 4 ? 3 : 2)
     if (threadIdx.x == 0) {
       for (int i = 0; i < 2; ++i) {
         const int zi = zs + i;
-        if (zi < ze && zi >= 0 && zi < nz) {
+        if (zi < ze && zi >= 0 && zi < nz && !B.no_copies) {
           mbar_expect_tx(smem_u32(&bar[i]), T::BOX_BYTES);
           tma_load_3d(smem_u32(raw_bytes + i * RAW_STRIDE), &V.tmap, tx0 - 8, ty0 - R, zi,
                       smem_u32(&bar[i]));
@@ -318,9 +319,9 @@ __global__ void __launch_bounds__(256, R <= 4 ? 3 : 2)
       if (threadIdx.x == 0) {
         atomicExch(B.status, 1);
         if (TMA) {
-          mbar_wait(smem_u32(&bar[b]), ((phase >> b) & 1u) ^ 1u);
+          if (!B.no_copies) mbar_wait(smem_u32(&bar[b]), ((phase >> b) & 1u) ^ 1u);
           const int zn = zi + 1;
-          if (zn < ze && zn >= 0 && zn < nz)
+          if (zn < ze && zn >= 0 && zn < nz && !B.no_copies)
             mbar_wait(smem_u32(&bar[b ^ 1]), (phase >> (b ^ 1)) & 1u);
         }
       }
@@ -329,7 +330,7 @@ __global__ void __launch_bounds__(256, R <= 4 ? 3 : 2)
     // raw[b] is consumed: fetch the slice two ahead into it.
     if (TMA && threadIdx.x == 0) {
       const int zn = zi + 2;
-      if (zn < ze && zn >= 0 && zn < nz) {
+      if (zn < ze && zn >= 0 && zn < nz && !B.no_copies) {
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         mbar_expect_tx(smem_u32(&bar[b]), T::BOX_BYTES);
         tma_load_3d(smem_u32(raw_bytes + b * RAW_STRIDE), &V.tmap, tx0 - 8, ty0 - R, zn,
@@ -508,7 +509,7 @@ cudaError_t smooth_status_word(int** p) {
   return cudaGetSymbolAddress((void**)p, g_smooth_status);
 }
 
-cudaError_t launch_smooth(const aug_smooth_desc* h, int n, cudaStream_t st) {
+cudaError_t launch_smooth(const aug_smooth_desc* h, int n, cudaStream_t st, bool no_copies) {
   int* status = nullptr;
   cudaError_t e = smooth_status_word(&status);
   if (e != cudaSuccess) return e;
@@ -540,6 +541,7 @@ cudaError_t launch_smooth(const aug_smooth_desc* h, int n, cudaStream_t st) {
     for (size_t g0 = 0; g0 < order.size(); g0 += kSmMaxVols) {
       SmoothBatch* Bt = new SmoothBatch;  // ~12 KB: off the host stack
       Bt->n = 0;
+      Bt->no_copies = no_copies ? 1 : 0;
       Bt->status = status;
       Bt->tile_start[0] = 0;
       for (int r = 0; r < 3; ++r) gauss_weights(h[b0].sigma[r], Bt->w[r]);

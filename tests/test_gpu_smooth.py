@@ -117,3 +117,21 @@ def test_argument_errors():
     with pytest.raises(A.AugError) as e:
         A.aug_smooth([img], [img], [(1.0, 1.0, 1.0)])      # in place
     assert e.value.status == A.AUG_ERR_INVALID_ARG
+
+
+def test_bounded_wait_runs_out_and_is_reported():
+    """No tile copy is issued: the block's wait for its first tile runs out
+    (after about a second), status 1 is recorded and the block returns; the
+    context stays usable and a normal call afterwards reports 0."""
+    import time
+    A = G.aw()
+    img = torch.zeros((8, 16, 64), dtype=torch.int16, device="cuda")   # one 64x16 tile, TMA path
+    out = torch.zeros((8, 16, 64), device="cuda")
+    assert A.aug_smooth_status() == 0
+    t0 = time.time()
+    A.aug_test_smooth_wait_timeout([img], [out], [(0.5, 0.5, 0.5)])
+    torch.cuda.synchronize()
+    assert A.aug_smooth_status() == 1
+    assert time.time() - t0 < 60.0
+    outs = run([img], [(0.5, 0.5, 0.5)])
+    assert np.all(np.isfinite(outs[0]))
