@@ -94,6 +94,9 @@ aug_status fwd_host_pipeline(const aug_volume_desc* h, int n, uint64_t seed, int
     const int k = std::min(chunk, n - c * chunk);
     slot = std::max(slot, chunk_bytes(h + c * chunk, k, ws));
   }
+  // A previous call's descriptor copies may still read the staging array.
+  for (int s = 0; s < kSlots; ++s)
+    if (cudaEventSynchronize(P->done[s]) != cudaSuccess) return AUG_ERR_CUDA;
   // Page-locked staging for every chunk's device descriptors (each copy reads
   // its own part, so no part is rewritten while a copy may still read it).
   if (P->h_cap < (size_t)n) {
@@ -104,23 +107,23 @@ aug_status fwd_host_pipeline(const aug_volume_desc* h, int n, uint64_t seed, int
       return AUG_ERR_CUDA;
     P->h_cap = (size_t)n;
   }
-  // A previous call's staging may still be read by copies in flight.
-  for (int s = 0; s < kSlots; ++s)
-    if (cudaEventSynchronize(P->done[s]) != cudaSuccess) return AUG_ERR_CUDA;
 
   const int n_slots = std::min(kSlots, n_chunks);
   char* buf[kSlots] = {};
-  for (int s = 0; s < n_slots; ++s)
-    if (cudaMallocAsync((void**)&buf[s], slot, stream) != cudaSuccess) return AUG_ERR_CUDA;
-  if (cudaEventRecord(P->ready, stream) != cudaSuccess) return AUG_ERR_CUDA;
   for (int s = 0; s < n_slots; ++s) {
-    if (cudaStreamWaitEvent(P->st[s], P->ready, 0) != cudaSuccess) return AUG_ERR_CUDA;
+    if (cudaMallocAsync((void**)&buf[s], slot, stream) != cudaSuccess) {
+      for (int t = 0; t < s; ++t) cudaFreeAsync(buf[t], stream);
+      return AUG_ERR_CUDA;
+    }
+  }
+  cudaError_t e = cudaEventRecord(P->ready, stream);
+  for (int s = 0; s < n_slots && e == cudaSuccess; ++s) {
+    e = cudaStreamWaitEvent(P->st[s], P->ready, 0);
     // The workspace's status header starts cleared.
     char* wsp = buf[s] + up256((size_t)chunk * sizeof(aug_volume_desc));
-    if (cudaMemsetAsync(wsp, 0, 256, P->st[s]) != cudaSuccess) return AUG_ERR_CUDA;
+    if (e == cudaSuccess) e = cudaMemsetAsync(wsp, 0, 256, P->st[s]);
   }
 
-  cudaError_t e = cudaSuccess;
   for (int c = 0; c < n_chunks && e == cudaSuccess; ++c) {
     const int s = c % kSlots, v0 = c * chunk, k = std::min(chunk, n - v0);
     cudaStream_t st = P->st[s];
