@@ -65,7 +65,7 @@ typedef enum {
   AUG_ERR_CUDA = 2,        /* a CUDA runtime call or kernel launch failed       */
   AUG_ERR_WORKSPACE = 3,   /* workspace NULL, misaligned or too small           */
   AUG_ERR_DESCRIPTOR = 4,  /* (device status) a volume descriptor is invalid    */
-  AUG_ERR_UNSUPPORTED = 5  /* valid request outside what this build implements  */
+  AUG_ERR_UNSUPPORTED = 5  /* valid request outside what this library implements */
 } aug_status;
 
 typedef enum { AUG_F32 = 0, AUG_I16 = 1 } aug_dtype;

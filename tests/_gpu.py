@@ -1,7 +1,7 @@
 """Helpers of the GPU parity tests: run the CUDA path through the C ABI on
 synthetic cases and compare with the FP64 oracle at the stated tolerances.
 
-Tolerances (fixed by the benchmark spec of the method):
+Tolerances of the parity checks:
 * image: |gpu - oracle| <= 2e-3 HU absolute;
 * labels: bit-exact except voxels whose FP64 source coordinate lies within
   1e-5 of a rounding tie (counted and reported);
