@@ -581,7 +581,7 @@ def bench_loss_variants(args, A, dev, stream):
 
 def bench_train(args, A, dev, stream, seed):
     from synth import workloads
-    w = workloads.config4(device=dev)
+    w = workloads.config4(device=dev, n_vols=args.train_vols)
     vols = w.vols
     out = [torch.empty(tuple(reversed(v.out_shape)), device=dev) for v in vols]
     batch = A.VolumeBatch([v.image for v in vols], np.stack([v.T for v in vols]),
@@ -612,7 +612,8 @@ def bench_train(args, A, dev, stream, seed):
     log(f"[train] {ms:.4f} ms/step")
     return {"value": round(n_out / (ms * 1e-3) / 1e9, 3), "unit": "Gvox/s",
             "ms_per_step": round(ms, 4), "alg_GBps": round(alg / (ms * 1e-3) / 1e9, 1),
-            "workload": "16 int16 512^2 x 300-600 -> 128x128x160: fwd + IOU fwd/bwd + grad_T"}
+            "workload": f"{len(vols)} int16 512^2 x 300-600 -> 128x128x160: fwd + IOU fwd/bwd + "
+                        "grad_T"}
 
 
 def bench_smooth(args, A, dev, stream):
@@ -721,6 +722,8 @@ def main():
     ap.add_argument("--autotune", action="store_true",
                     help="pick the forward variant by timing all of them first")
     ap.add_argument("--no-preroll", action="store_true")
+    ap.add_argument("--train-vols", type=int, default=16,
+                    help="volumes of the training-step workload (profiling runs use fewer)")
     ap.add_argument("--smooth-vols", type=int, default=16,
                     help="volumes of the smoothing workload (profiling runs use fewer)")
     args = ap.parse_args()
