@@ -332,6 +332,19 @@ def run_ours(args, rank, world, local):
                         "ms_per_step": round(ms_plain, 4), "launches_per_step": batch.n}
         log(f"[plain] {ms_plain:.4f} ms/step")
 
+        # ---- the hardware-texture alternative (tex3D linear filtering), same batch ------------
+        # A measured comparison only: its interpolation error is several HU (see the tests).
+        tw = A.TexWarp(batch.h_descs)
+        g_tex = capture(lambda: tw.run(seed), stream)
+        ms_tex = time_graph(g_tex, max(3, min(args.steps, 50)), args.warmup, stream)
+        del g_tex
+        tw.close()
+        res["tex3d"] = {"value": round(n_out / (ms_tex * 1e-3) / 1e9, 3), "unit": "Gvox/s",
+                        "ms_per_step": round(ms_tex, 4), "launches_per_step": batch.n,
+                        "note": "tex3D linear filtering on float32 coordinates, one launch per "
+                                "volume; not a parity path (error several HU)"}
+        log(f"[tex3d] {ms_tex:.4f} ms/step")
+
         # ---- end to end through the C ABI from pinned host buffers: aug_warp_fwd_host
         # copies each chunk of volumes in, augments it and copies it out, overlapping
         # the chunks (the host <-> device FIFO of Sec. 4) ---------------------------------
@@ -855,6 +868,7 @@ def main():
         "fwd_bwd": res["fwd_bwd"],
         "fwd_device_params": res.get("fwd_device_params"),
         "plain_fwd": res["plain"],
+        "tex3d_alternative": res.get("tex3d"),
         "e2e": res["e2e"],
         "gpu_launches": res["launches"],
         "clocks": res["clocks"],

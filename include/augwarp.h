@@ -276,6 +276,27 @@ aug_status aug_test_smooth_wait_timeout(const aug_smooth_desc* h_descs, int n_vo
 aug_status aug_warp_fwd_host(const aug_volume_desc* h_descs, int n_vols, uint64_t seed,
                              int chunk_vols, aug_stream_t stream);
 
+/* ---- hardware-texture alternative (a measured comparison) -----------------------
+ * The paper's own sampling (Sec. 4): trilinear interpolation by the texture
+ * unit (tex3D, linear filtering, fixed-point weights) on float32 coordinates.
+ * It is not a parity path: its interpolation error is several HU at sharp
+ * edges, far above the exact path's 2e-3 HU.  The intensity affine and the noise
+ * are the exact path's (same Philox stream); labels are the nearest voxel.
+ *
+ * aug_tex_create: h_descs is a HOST array of n_vols descriptors (device
+ * buffers, float32 images); copies each image into a newly allocated 3-D CUDA
+ * array read through a texture whose border colour is fill_image; *handle
+ * receives an opaque handle owning them.  Synchronous.
+ * aug_tex_warp_fwd: writes each descriptor's out_image / out_label, one launch
+ * per volume on `stream`.  aug_tex_destroy frees the handle (after the
+ * launches that use it have finished).
+ * Errors: NULL arguments or n_vols outside 1..65535: AUG_ERR_INVALID_ARG; a
+ * descriptor failing the checks of aug_warp_fwd_volume: AUG_ERR_DESCRIPTOR;
+ * an int16 image with an image output, or flags != 0: AUG_ERR_UNSUPPORTED. */
+aug_status aug_tex_create(const aug_volume_desc* h_descs, int n_vols, void** handle);
+aug_status aug_tex_warp_fwd(void* handle, uint64_t seed, aug_stream_t stream);
+aug_status aug_tex_destroy(void* handle);
+
 /* ---- adjoint of the image warp ---------------------------------------------
  * For upstream gradients g_b (shape of out_image of volume b, float32):
  *   grad_in_b[n]    = sum_o photo_a g_b(o) w_{n}(o)       over in-volume taps,

@@ -74,6 +74,12 @@ def _load():
     L.aug_sample_params.restype = i32
     L.aug_warp_fwd_host.argtypes = [vp, i32, u64, i32, vp]
     L.aug_warp_fwd_host.restype = i32
+    L.aug_tex_create.argtypes = [vp, i32, C.POINTER(vp)]
+    L.aug_tex_create.restype = i32
+    L.aug_tex_warp_fwd.argtypes = [vp, u64, vp]
+    L.aug_tex_warp_fwd.restype = i32
+    L.aug_tex_destroy.argtypes = [vp]
+    L.aug_tex_destroy.restype = i32
     L.aug_smooth.argtypes = [vp, i32, vp]
     L.aug_smooth.restype = i32
     L.aug_test_smooth_wait_timeout.argtypes = [vp, i32, vp]
@@ -208,6 +214,29 @@ def host_descriptors(images, affines, out_shapes, labels=None, out_images=None, 
             assert not out_labels[b].is_cuda and tuple(out_labels[b].shape) == (onz, ony, onx)
             h["out_label"][b] = out_labels[b].data_ptr()
     return h
+
+
+class TexWarp:
+    """The hardware-texture alternative of the forward (tex3D linear filtering,
+    a measured comparison, not a parity path): built from host descriptors
+    (device buffers, float32 images), run with ``run(seed)``, freed by
+    ``close()``."""
+
+    def __init__(self, h_descs: np.ndarray):
+        self._h = np.ascontiguousarray(h_descs, dtype=DESC_DTYPE)
+        self._handle = C.c_void_p()
+        _check(_L.aug_tex_create(self._h.ctypes.data_as(C.c_void_p), len(self._h),
+                                 C.byref(self._handle)), "aug_tex_create")
+
+    def run(self, seed: int, stream=None):
+        _check(_L.aug_tex_warp_fwd(self._handle, _seed(seed), _stream(stream)),
+               "aug_tex_warp_fwd")
+
+    def close(self):
+        if self._handle:
+            torch.cuda.synchronize()
+            _L.aug_tex_destroy(self._handle)
+            self._handle = C.c_void_p()
 
 
 def aug_warp_bwd(d_descs: torch.Tensor, n_vols: int, d_grad_out_ptrs: torch.Tensor,

@@ -404,6 +404,25 @@ float aug_antialias_sigma(float r, float u) {
   return (float)((t > 0.0 ? t : 0.0) / 3.0);
 }
 
+aug_status aug_tex_create(const aug_volume_desc* h_descs, int n_vols, void** handle) {
+  if (h_descs == nullptr || handle == nullptr || n_vols < 1 || n_vols > kMaxVols)
+    return AUG_ERR_INVALID_ARG;
+  for (int b = 0; b < n_vols; ++b) {
+    if (!host_desc_ok(h_descs[b])) return AUG_ERR_DESCRIPTOR;
+    if (h_descs[b].flags != 0) return AUG_ERR_UNSUPPORTED;
+    if (h_descs[b].out_image != nullptr && h_descs[b].image_dtype != AUG_F32)
+      return AUG_ERR_UNSUPPORTED;
+  }
+  return tex_create(h_descs, n_vols, handle);
+}
+
+aug_status aug_tex_warp_fwd(void* handle, uint64_t seed, aug_stream_t stream) {
+  if (handle == nullptr) return AUG_ERR_INVALID_ARG;
+  return tex_warp_fwd(handle, seed, (cudaStream_t)stream);
+}
+
+aug_status aug_tex_destroy(void* handle) { return tex_destroy(handle); }
+
 int aug_num_variants(int op) { return n_variants(op); }
 
 const char* aug_variant_name(int op, int variant) {

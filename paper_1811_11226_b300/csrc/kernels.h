@@ -63,6 +63,11 @@ size_t fwd_workspace_bytes(int n_vols);
 aug_status fwd_host_pipeline(const aug_volume_desc* h, int n, uint64_t seed, int chunk,
                              cudaStream_t stream);
 
+// Hardware-texture alternative of the forward (measured comparison).
+aug_status tex_create(const aug_volume_desc* h, int n, void** handle);
+aug_status tex_warp_fwd(void* handle, uint64_t seed, cudaStream_t st);
+aug_status tex_destroy(void* handle);
+
 cudaError_t launch_philox(const uint32_t* ctr, long long n, unsigned k0, unsigned k1,
                           uint32_t* out, cudaStream_t st);
 
