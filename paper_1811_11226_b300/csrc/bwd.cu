@@ -29,7 +29,7 @@ struct BrickMap {
   int bsy, bsz, boff;
 };
 
-template <typename TIn, int MODE, bool GIN, bool GT, bool SMEM>
+template <typename TIn, int MODE, bool GIN, bool GT, bool SMEM, bool XM = false>
 __device__ __forceinline__ void bwd_run(const VolConst& vc, const TileCoord& tc, long long sx,
                                         long long sy, long long sz,
                                         const float* __restrict__ g, float* __restrict__ gin,
@@ -57,7 +57,10 @@ __device__ __forceinline__ void bwd_run(const VolConst& vc, const TileCoord& tc,
     const float ga = (tc.valid && !occ) ? a * __ldcs(g + o) : 0.0f;
     Taps t;
     load_taps<TIn, MODE>(img, sx, sy, sz, nx, ny, nz, fill, t);
-    if (GIN && tc.valid) {
+    // With XM the interior branch runs in every lane of the warp (its shuffles
+    // need them all); lanes outside the output only carry zeros and never
+    // issue a reduction.
+    if (GIN && (tc.valid || (XM && MODE == MODE_INTERIOR))) {
       const float wx1 = t.tx, wx0 = 1.0f - t.tx, wy1 = t.ty, wy0 = 1.0f - t.ty;
       const float wz1 = t.tz, wz0 = 1.0f - t.tz;
       const float g00 = ga * wy0 * wz0, g10 = ga * wy1 * wz0;
@@ -71,7 +74,7 @@ __device__ __forceinline__ void bwd_run(const VolConst& vc, const TileCoord& tc,
           c1 += pend[1];
           c2 += pend[2];
           c3 += pend[3];
-        } else if (pend_base >= 0) {
+        } else if (pend_base >= 0 && tc.valid) {
           float* q = tgt + pend_base;
           RADD(q, pend[0]);
           RADD(q + 1, pend[1]);
@@ -79,10 +82,35 @@ __device__ __forceinline__ void bwd_run(const VolConst& vc, const TileCoord& tc,
           RADD(q + sy_ + 1, pend[3]);
         }
         float* p = tgt + base;
-        RADD(p, c0);
-        RADD(p + 1, c1);
-        RADD(p + sy_, c2);
-        RADD(p + sy_ + 1, c3);
+        if (XM) {
+          // Merge along x: when the next lane's cell is this one moved by +1
+          // in x, this lane's x+1 taps are its x taps; hand the two values
+          // over instead of issuing them.
+          const int lane = threadIdx.x & 31;
+          const int nb = __shfl_down_sync(FULL_MASK, base, 1);
+          const int nv = __shfl_down_sync(FULL_MASK, (int)tc.valid, 1);
+          const bool give = tc.valid && lane < 31 && nv && nb == base + 1;
+          const float l1 = __shfl_up_sync(FULL_MASK, c1, 1);
+          const float l3 = __shfl_up_sync(FULL_MASK, c3, 1);
+          const int lg = __shfl_up_sync(FULL_MASK, (int)give, 1);
+          if (lane > 0 && lg) {
+            c0 += l1;
+            c2 += l3;
+          }
+          if (tc.valid) {
+            RADD(p, c0);
+            RADD(p + sy_, c2);
+            if (!give) {
+              RADD(p + 1, c1);
+              RADD(p + sy_ + 1, c3);
+            }
+          }
+        } else {
+          RADD(p, c0);
+          RADD(p + 1, c1);
+          RADD(p + sy_, c2);
+          RADD(p + sy_ + 1, c3);
+        }
         pend[0] = g01 * wx0;
         pend[1] = g01 * wx1;
         pend[2] = g11 * wx0;
@@ -129,7 +157,7 @@ __device__ __forceinline__ void bwd_run(const VolConst& vc, const TileCoord& tc,
     sz += dz;
     o += plane;
   }
-  if (GIN && MODE == MODE_INTERIOR && pend_base >= 0) {
+  if (GIN && MODE == MODE_INTERIOR && pend_base >= 0 && tc.valid) {
     float* q = tgt + pend_base;
     RADD(q, pend[0]);
     RADD(q + 1, pend[1]);
@@ -145,7 +173,7 @@ struct BwdShared {
   double acc[12];
 };
 
-template <typename TIn, int NW, int QZ, bool GIN, bool GT, bool SMEM = false>
+template <typename TIn, int NW, int QZ, bool GIN, bool GT, bool SMEM = false, bool XM = false>
 __device__ __forceinline__ void bwd_tile(const VolConst& vc, BwdShared<NW>& sh, int t,
                                          const float* g, float* gin,
                                          const BrickMap& bm = BrickMap{nullptr, 0, 0, 0}) {
@@ -161,7 +189,7 @@ __device__ __forceinline__ void bwd_tile(const VolConst& vc, BwdShared<NW>& sh, 
       warp_mode(classify_run<true>(s, ds, tc.k1 - 1 - tc.k0, vc.nx, vc.ny, vc.nz));
   // Exterior cells have all taps equal to the fill value: no gradient at all.
   if (mode == MODE_INTERIOR)
-    bwd_run<TIn, MODE_INTERIOR, GIN, GT, SMEM>(vc, tc, s[0], s[1], s[2], g, gin, bm, acc);
+    bwd_run<TIn, MODE_INTERIOR, GIN, GT, SMEM, XM>(vc, tc, s[0], s[1], s[2], g, gin, bm, acc);
   else if (mode == MODE_GENERAL)
     bwd_run<TIn, MODE_GENERAL, GIN, GT, SMEM>(vc, tc, s[0], s[1], s[2], g, gin, bm, acc);
   if (GT) {
@@ -191,7 +219,7 @@ __device__ __forceinline__ void bwd_tile(const VolConst& vc, BwdShared<NW>& sh, 
   }
 }
 
-template <int NW, int QZ, bool GIN, bool GT>
+template <int NW, int QZ, bool GIN, bool GT, bool XM = false>
 __global__ void __launch_bounds__(NW * 32, 1024 / (NW * 32))
     k_bwd_batched(const aug_volume_desc* __restrict__ descs, int n_vols,
                   const VolConst* __restrict__ tab, const float* const* gout,
@@ -226,9 +254,9 @@ __global__ void __launch_bounds__(NW * 32, 1024 / (NW * 32))
         const float* g = gout[v];
         float* gi = GIN ? gin[v] : nullptr;
         if (vc.dtype == AUG_I16)
-          bwd_tile<int16_t, NW, QZ, GIN, GT>(vc, sh, t, g, gi);
+          bwd_tile<int16_t, NW, QZ, GIN, GT, false, XM>(vc, sh, t, g, gi);
         else
-          bwd_tile<float, NW, QZ, GIN, GT>(vc, sh, t, g, gi);
+          bwd_tile<float, NW, QZ, GIN, GT, false, XM>(vc, sh, t, g, gi);
       });
   flush();
 }
@@ -396,14 +424,22 @@ struct BwdVariant {
         {k_bwd_batched<NW, QZ, false, false>, k_bwd_batched<NW, QZ, false, true>,      \
          k_bwd_smem<NW, QZ, false, CAP>, k_bwd_smem<NW, QZ, true, CAP> }               \
   }
+#define BWD_X(NW, QZ)                                                                  \
+  {                                                                                    \
+    NW, QZ, 0,                                                                         \
+        {k_bwd_batched<NW, QZ, false, false>, k_bwd_batched<NW, QZ, false, true>,      \
+         k_bwd_batched<NW, QZ, true, false, true>, k_bwd_batched<NW, QZ, true, true, true> } \
+  }
 const BwdVariant kBwd[] = {BWD_V(8, 4),         BWD_V(4, 4),        BWD_V(8, 2),
                            BWD_V(8, 8),         BWD_S(16, 2, 24576), BWD_S(8, 2, 16384),
-                           BWD_S(8, 4, 24576)};
+                           BWD_S(8, 4, 24576),  BWD_X(8, 4),        BWD_X(8, 8)};
 #undef BWD_V
 #undef BWD_S
+#undef BWD_X
 const char* kBwdNames[] = {"t32x8x16_atomic",   "t32x4x16_atomic",  "t32x8x8_atomic",
                            "t32x8x32_atomic",   "t32x16x8_brick96k", "t32x8x8_brick64k",
-                           "t32x8x16_brick96k"};
+                           "t32x8x16_brick96k", "t32x8x16_atomic_xmerge",
+                           "t32x8x32_atomic_xmerge"};
 }  // namespace
 
 int bwd_num_variants() { return (int)(sizeof(kBwd) / sizeof(kBwd[0])); }
