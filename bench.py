@@ -312,22 +312,14 @@ def run_ours(args, rank, world, local):
             f"{achieved:.0f} GB/s algorithmic ({alg / 1e9:.3f} GB/step)")
 
     if args.only == "all":
-        # ---- plain one-volume-per-launch forward on the same batch ---------------------------
+        # ---- plain one-volume-per-launch forward on the same batch (the 64 launches
+        # captured in one graph, so that host launch overhead is not timed) ---------------
         def plain():
             for b in range(batch.n):
                 A.aug_warp_fwd_volume(batch.h_descs[b:b + 1], seed)
-        with torch.cuda.stream(stream):
-            for _ in range(3):
-                plain()
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            reps = max(3, min(args.steps, 50))
-            e0.record(stream)
-            for _ in range(reps):
-                plain()
-            e1.record(stream)
-            e1.synchronize()
-        ms_plain = e0.elapsed_time(e1) / reps
+        g_plain = capture(plain, stream)
+        ms_plain = time_graph(g_plain, max(3, min(args.steps, 50)), args.warmup, stream)
+        del g_plain
         res["plain"] = {"value": round(n_out / (ms_plain * 1e-3) / 1e9, 3), "unit": "Gvox/s",
                         "ms_per_step": round(ms_plain, 4), "launches_per_step": batch.n}
         log(f"[plain] {ms_plain:.4f} ms/step")
