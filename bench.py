@@ -73,27 +73,30 @@ def kernel_source_hash():
     return h.hexdigest()[:16]
 
 
-def profile_record(name, key):
+def profile_record(name, key, variant=None):
     """A per-launch figure recorded in profiles/<name>.md from an ncu capture
-    ('<key>: N' beside 'csrc_hash: H'); None if absent or if the kernel's
-    sources changed since the capture."""
+    ('<key>: N' beside 'csrc_hash: H' and 'variant: V'); None if absent, if the
+    kernel's sources changed since the capture, or if the capture was of
+    another kernel variant than the one timed."""
     p = os.path.join(ROOT, "profiles", f"{name}.md")
     if not os.path.exists(p):
         return None
     kv = {}
     for line in open(p):
         line = line.strip().lstrip("-* ")
-        if ":" in line and line.startswith((key, "csrc_hash")):
+        if ":" in line and line.startswith((key, "csrc_hash", "variant")):
             k, v = line.split(":", 1)
             kv[k.strip()] = v.strip().strip("`")
     if kv.get("csrc_hash") != kernel_source_hash() or key not in kv:
         return None
+    if variant is not None and kv.get("variant") != variant:
+        return None
     return float(kv[key])
 
 
-def profile_traffic(name):
+def profile_traffic(name, variant=None):
     """DRAM bytes per launch of the recorded capture (see profile_record)."""
-    return profile_record(name, "dram_bytes_per_launch")
+    return profile_record(name, "dram_bytes_per_launch", variant)
 
 
 class ClockSampler:
@@ -828,7 +831,7 @@ def main():
     if world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline()
     peak = res["peak"]
-    traffic = profile_traffic("fwd_batched_config1")
+    traffic = profile_traffic("fwd_batched_config1", res["variant"])
     line = {
         "metric": METRIC,
         "value": round(res["value"], 3),
@@ -874,7 +877,7 @@ def main():
 
 
 def issue_roofline(res):
-    inst = profile_record("fwd_batched_config1", "warp_inst_per_launch")
+    inst = profile_record("fwd_batched_config1", "warp_inst_per_launch", res["variant"])
     sm_mhz = (res.get("clocks") or {}).get("sm_mhz")
     if inst is None or not sm_mhz:
         return None

@@ -122,10 +122,11 @@ __device__ __forceinline__ int q40_floor(long long s) { return q40_hi(s) >> 8; }
 __device__ __forceinline__ int q40_round(long long s) { return (q40_hi(s) + 128) >> 8; }
 // s - floor(s), truncated to 23 bits (error < 2^-23): the top 23 fractional
 // bits become the mantissa of a float in [1, 2), minus 1 (exact).
-__device__ __forceinline__ float q40_frac(long long s) {
+__device__ __forceinline__ float q40_one_plus_frac(long long s) {
   const unsigned m = (unsigned)((unsigned long long)s >> 17) & 0x7FFFFFu;
-  return __uint_as_float(0x3F800000u | m) - 1.0f;
+  return __uint_as_float(0x3F800000u | m);
 }
+__device__ __forceinline__ float q40_frac(long long s) { return q40_one_plus_frac(s) - 1.0f; }
 // Bit 39 of s: 1 when frac(s) >= 1/2, i.e. floor(s + 1/2) = floor(s) + bit.
 __device__ __forceinline__ int q40_halfbit(long long s) { return (q40_hi(s) >> 7) & 1; }
 
@@ -202,12 +203,14 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, unsigned k0, unsigned k1
   return c;
 }
 
-// The ten round keys of a Philox4x32-10 key, computed once (they depend only
-// on the seed, so a kernel computes them at entry, where they are uniform).
+// The ten round keys of a Philox4x32-10 key.  They depend only on the seed:
+// the host computes them and passes them to the noise kernels as a by-value
+// parameter, so each round's XOR reads its key from the constant bank instead
+// of recomputing k + r * Weyl in registers on every call.
 struct PhiloxKey {
   unsigned k0[10], k1[10];
 };
-__device__ __forceinline__ PhiloxKey philox_schedule(unsigned k0, unsigned k1) {
+__host__ __device__ __forceinline__ PhiloxKey philox_schedule(unsigned k0, unsigned k1) {
   PhiloxKey k;
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
@@ -244,19 +247,27 @@ __device__ __forceinline__ float ex2_approx(float x) {
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
-__device__ __forceinline__ float sqrt_approx(float x) {
+// Flush-to-zero forms, for arguments that are never subnormal: they give the
+// same results as the plain forms there and skip the subnormal fix-up code
+// that the plain forms carry around the hardware instruction.
+__device__ __forceinline__ float lg2_approx_ftz(float x) {
   float r;
-  asm("sqrt.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
-__device__ __forceinline__ float sin_approx(float x) {
+__device__ __forceinline__ float sqrt_approx_ftz(float x) {
   float r;
-  asm("sin.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
-__device__ __forceinline__ float cos_approx(float x) {
+__device__ __forceinline__ float sin_approx_ftz(float x) {
   float r;
-  asm("cos.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  asm("sin.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float cos_approx_ftz(float x) {
+  float r;
+  asm("cos.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
 
@@ -265,7 +276,7 @@ __device__ __forceinline__ float cos_approx(float x) {
 // R = sqrt(-2 ln u1).
 //
 // -2 ln u1: for v = 1 - u1 < 2^-6 (exact in float) the series
-// 2 v (1 + v/2 + v^2/3) (Taylor series of -2 ln(1 - v), relative truncation
+// v (2 + v (1 + 2v/3)) (Taylor series of -2 ln(1 - v), relative truncation
 // error < v^3/2 < 2e-6, i.e. < 2e-7 absolute on R <= 0.18) keeps full
 // accuracy where R is small; otherwise -2 ln 2 * log2(u1) with the hardware log2 (absolute error
 // ~2^-22), which changes R by < 1e-6 there since R > 0.17.  R uses the
@@ -273,15 +284,19 @@ __device__ __forceinline__ float cos_approx(float x) {
 // a = 2 pi u2 - pi in [-pi, pi), where the hardware sine/cosine have absolute
 // error ~2^-21, and cos(2 pi u2) = -cos a, sin(2 pi u2) = -sin a.  Overall
 // |n - n_exact| < ~5e-6 for |n| <= 5.8, i.e. < 2.5e-4 HU at sigma = 50.
+// No argument of the hardware functions is subnormal (u1 >= 2^-24; x is 0 or
+// >= 2^-23; a is 0 or |a| >= 2^-22), so their flush-to-zero forms are exact
+// stand-ins for the plain ones.
 __device__ __forceinline__ float2 box_muller(unsigned ra, unsigned rb) {
   const unsigned m1 = ra >> 8, m2 = rb >> 8;
   const float u1 = (float)(m1 + 1u) * 5.9604644775390625e-8f;
   const float v = 1.0f - u1;  // exact: u1 lies on the 2^-24 grid of (0, 1]
-  const float series = 2.0f * v * fmaf(v, fmaf(v, 0.333333333f, 0.5f), 1.0f);
-  const float x = (v < 0.015625f) ? series : -1.38629436112f * lg2_approx(u1);
-  const float r = sqrt_approx(x);
-  const float a = fmaf((float)m2 * 5.9604644775390625e-8f, 6.28318530718f, -3.14159265359f);
-  return make_float2(-r * cos_approx(a), -r * sin_approx(a));
+  const float series = v * fmaf(v, fmaf(v, 0.666666667f, 1.0f), 2.0f);
+  const float x = (v < 0.015625f) ? series : -1.38629436112f * lg2_approx_ftz(u1);
+  const float r = sqrt_approx_ftz(x);
+  // (m2 2^-24) 2 pi rounds like m2 (2 pi 2^-24): scaling by 2^-24 is exact.
+  const float a = fmaf((float)m2, 6.28318530718f * 5.9604644775390625e-8f, -3.14159265359f);
+  return make_float2(-r * cos_approx_ftz(a), -r * sin_approx_ftz(a));
 }
 
 // Four normals of one quad (lanes 0..3).

@@ -244,7 +244,7 @@ __device__ __forceinline__ void fwd_quads(const FwdP<TIn>& P, const TileCoord& t
 
 template <typename TIn, int NW, int QZ, int PD, bool IMG, bool LAB>
 __device__ __forceinline__ void fwd_tile_t(const VolConst& vc, int t, const PhiloxKey& key) {
-  const TileCoord tc = tile_coord<NW, QZ>(t, vc.onx, vc.ony, vc.onz);
+  const TileCoord tc = tile_coord_flat<NW, QZ>(t, vc.onx, vc.ony, vc.onz);
   FwdP<TIn> P;
   P.img = (const TIn*)vc.image;
   P.lab = vc.label;
@@ -342,10 +342,9 @@ __device__ __forceinline__ void fwd_tile(const VolConst& vc, int t, const Philox
 template <int NW, int QZ, int MB, int PD>
 __global__ void __launch_bounds__(NW * 32, MB)
     k_fwd_batched(const aug_volume_desc* __restrict__ descs, int n_vols,
-                  const VolConst* __restrict__ tab, unsigned key0, unsigned key1) {
+                  const VolConst* __restrict__ tab, const PhiloxKey key) {
   __shared__ SchedSmem<NW * 32> sm;
-  const PhiloxKey key = philox_schedule(key0, key1);
-  for_each_tile<NW, QZ>(
+  for_each_tile<NW, QZ, true>(
       descs, n_vols, sm, [](int, int) {},
       [&](int v, int t, long long) {
         const VolConst& vc = tab[v];
@@ -356,18 +355,18 @@ __global__ void __launch_bounds__(NW * 32, MB)
 
 template <int NW, int QZ, int MB, int PD>
 __global__ void __launch_bounds__(NW * 32, MB)
-    k_fwd_volume(const aug_volume_desc desc, unsigned key0, unsigned key1) {
+    k_fwd_volume(const aug_volume_desc desc, const PhiloxKey key) {
   __shared__ VolConst vc;
   if (threadIdx.x == 0) make_volconst(desc, desc_valid(desc, desc.out_image != nullptr, false), vc);
   __syncthreads();
   if (!vc.ok) return;
-  fwd_tile<NW, QZ, PD>(vc, blockIdx.x, philox_schedule(key0, key1));
+  fwd_tile<NW, QZ, PD>(vc, blockIdx.x, key);
 }
 
 // ---- host launchers ----------------------------------------------------------
 namespace {
-using FwdBK = void (*)(const aug_volume_desc*, int, const VolConst*, unsigned, unsigned);
-using FwdVK = void (*)(const aug_volume_desc, unsigned, unsigned);
+using FwdBK = void (*)(const aug_volume_desc*, int, const VolConst*, const PhiloxKey);
+using FwdVK = void (*)(const aug_volume_desc, const PhiloxKey);
 struct FwdVariant {
   int nw, qz;
   FwdBK batched;
@@ -379,12 +378,12 @@ struct FwdVariant {
 const FwdVariant kFwd[] = {FWD_V(4, 8, 8, 2),  FWD_V(4, 8, 1, 2),  FWD_V(4, 8, 6, 4),
                            FWD_V(4, 8, 8, 1),  FWD_V(4, 8, 12, 1), FWD_V(4, 8, 10, 2),
                            FWD_V(8, 4, 4, 1),  FWD_V(8, 4, 6, 1),  FWD_V(8, 4, 4, 2),
-                           FWD_V(4, 4, 12, 1), FWD_V(2, 8, 16, 1)};
+                           FWD_V(4, 4, 12, 1), FWD_V(2, 8, 16, 1), FWD_V(4, 8, 9, 2)};
 #undef FWD_V
 const char* kFwdNames[] = {"t32x4x32_pd2_32w", "t32x4x32_pd2",     "t32x4x32_pd4_24w",
                            "t32x4x32_pd1_32w", "t32x4x32_pd1_48w", "t32x4x32_pd2_40w",
                            "t32x8x16_pd1_32w", "t32x8x16_pd1_48w", "t32x8x16_pd2_32w",
-                           "t32x4x16_pd1_48w", "t32x2x32_pd1_32w"};
+                           "t32x4x16_pd1_48w", "t32x2x32_pd1_32w", "t32x4x32_pd2_36w"};
 }  // namespace
 
 int fwd_num_variants() { return (int)(sizeof(kFwd) / sizeof(kFwd[0])); }
@@ -399,18 +398,19 @@ cudaError_t launch_fwd_batched(int variant, const aug_volume_desc* d, int n, uns
   cudaError_t e = launch_prepare(d, n, NEED_IMAGE_IF_OUT, false, nullptr, nullptr, false, tab, ws,
                                  st);
   if (e != cudaSuccess) return e;
-  fv.batched<<<grid, block, 0, st>>>(d, n, tab, k0, k1);
+  fv.batched<<<grid, block, 0, st>>>(d, n, tab, philox_schedule(k0, k1));
   return cudaGetLastError();
 }
 
 cudaError_t launch_fwd_volume(int variant, const aug_volume_desc& h, unsigned k0, unsigned k1,
                               cudaStream_t st) {
   const FwdVariant& fv = kFwd[variant];
-  const long long tiles = (long long)((h.out_nx + 31) / 32) *
-                          ((h.out_ny + fv.nw - 1) / fv.nw) *
+  // Flat plane mapping (tile_coord_flat): NW*32 plane positions x 4*QZ slices.
+  const long long plane = (long long)h.out_nx * h.out_ny;
+  const long long tiles = ((plane + fv.nw * 32 - 1) / (fv.nw * 32)) *
                           ((h.out_nz + 4 * fv.qz - 1) / (4 * fv.qz));
   if (tiles <= 0 || tiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  fv.volume<<<(unsigned)tiles, fv.nw * 32, 0, st>>>(h, k0, k1);
+  fv.volume<<<(unsigned)tiles, fv.nw * 32, 0, st>>>(h, philox_schedule(k0, k1));
   return cudaGetLastError();
 }
 

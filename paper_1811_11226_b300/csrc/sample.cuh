@@ -45,6 +45,34 @@ __device__ __forceinline__ TileCoord tile_coord(int t, int onx, int ony, int onz
   return c;
 }
 
+// Flat mapping (forward kernels): the tile's NW*32 threads take NW*32
+// consecutive positions p = j*onx + i of the output plane (thread-fastest),
+// times 4*QZ z values, so every warp is full whatever onx is (the 2-D tiles
+// above leave onx mod 32 lanes of a row's last tile idle).  A warp still
+// covers 32 memory-consecutive outputs, in at most two rows when onx >= 32.
+template <int NW, int QZ>
+__device__ __forceinline__ int tiles_in_flat(int onx, int ony, int onz) {
+  return ((onx * ony + NW * 32 - 1) / (NW * 32)) * ((onz + 4 * QZ - 1) / (4 * QZ));
+}
+
+template <int NW, int QZ>
+__device__ __forceinline__ TileCoord tile_coord_flat(int t, int onx, int ony, int onz) {
+  const int plane = onx * ony;
+  const int tp_n = (plane + NW * 32 - 1) / (NW * 32);
+  const int tp = t % tp_n, tz = t / tp_n;
+  const int p = tp * (NW * 32) + (int)threadIdx.x;
+  TileCoord c;
+  c.valid = p < plane;
+  const int pc = min(p, plane - 1);
+  c.jc = pc / onx;
+  c.ic = pc - c.jc * onx;
+  c.i = c.ic;
+  c.j = c.jc;
+  c.k0 = tz * 4 * QZ;
+  c.k1 = min(c.k0 + 4 * QZ, onz);
+  return c;
+}
+
 // Q.40 coordinate of output voxel (i, j, k) along one axis.
 __device__ __forceinline__ long long coord_q40(const long long (&tq)[4], int i, int j, int k) {
   return tq[0] * (long long)i + tq[1] * (long long)j + tq[2] * (long long)k + tq[3];

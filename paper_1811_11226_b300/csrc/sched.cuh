@@ -29,14 +29,17 @@ struct SchedSmem {
 };
 
 // Output dims of a descriptor if they are valid, else 0 tiles / 0 voxels (the
-// full descriptor check happens when the volume is staged).
-template <int NW, int QZ>
+// full descriptor check happens when the volume is staged).  FLAT: tiles of
+// the flat plane mapping (tile_coord_flat), else 32 x NW x 4*QZ boxes.
+template <int NW, int QZ, bool FLAT>
 __device__ __forceinline__ void volume_counts(const aug_volume_desc* d, int& tiles,
                                               long long& vox) {
   const int onx = d->out_nx, ony = d->out_ny, onz = d->out_nz;
   const bool ok = onx >= 1 && ony >= 1 && onz >= 1 && onx <= MAX_DIM && ony <= MAX_DIM &&
                   onz <= MAX_DIM && (long long)onx * ony * onz < (1LL << 31);
-  tiles = ok ? ((onx + 31) / 32) * ((ony + NW - 1) / NW) * ((onz + 4 * QZ - 1) / (4 * QZ)) : 0;
+  const int per_slab = FLAT ? (onx * ony + NW * 32 - 1) / (NW * 32)
+                            : ((onx + 31) / 32) * ((ony + NW - 1) / NW);
+  tiles = ok ? per_slab * ((onz + 4 * QZ - 1) / (4 * QZ)) : 0;
   vox = ok ? (long long)onx * ony * onz : 0;
 }
 
@@ -44,7 +47,7 @@ __device__ __forceinline__ void volume_counts(const aug_volume_desc* d, int& til
 // increasing global order, with all threads of the CTA together (body may
 // synchronise).  chunk_begin(c0, cnt) runs once per chunk before its tiles
 // (all threads; may synchronise), e.g. to zero per-volume partial sums.
-template <int NW, int QZ, typename ChunkF, typename BodyF>
+template <int NW, int QZ, bool FLAT = false, typename ChunkF, typename BodyF>
 __device__ __forceinline__ void for_each_tile(const aug_volume_desc* __restrict__ descs,
                                               int n_vols, SchedSmem<NW * 32>& sm,
                                               ChunkF&& chunk_begin, BodyF&& body) {
@@ -57,7 +60,7 @@ __device__ __forceinline__ void for_each_tile(const aug_volume_desc* __restrict_
     const int cnt = min(BLOCK, n_vols - c0);
     int t = 0;
     long long x = 0;
-    if ((int)threadIdx.x < cnt) volume_counts<NW, QZ>(descs + c0 + threadIdx.x, t, x);
+    if ((int)threadIdx.x < cnt) volume_counts<NW, QZ, FLAT>(descs + c0 + threadIdx.x, t, x);
     // Inclusive warp scan, then across warps.
     int ti = t;
     long long xi = x;

@@ -43,7 +43,7 @@ struct TexSet {
 constexpr int kTexNW = 4;
 
 __global__ void __launch_bounds__(kTexNW * 32)
-    k_tex_fwd(const TexVol V, unsigned key0, unsigned key1) {
+    k_tex_fwd(const TexVol V, const PhiloxKey key) {
   const int i = blockIdx.x * 32 + (threadIdx.x & 31);
   const int j = blockIdx.y * kTexNW + (threadIdx.x >> 5);
   const int kq = blockIdx.z * 4;
@@ -53,7 +53,7 @@ __global__ void __launch_bounds__(kTexNW * 32)
     const unsigned long long quad =
         ((unsigned long long)(kq >> 2) * (unsigned)V.ony + (unsigned)j) * (unsigned)V.onx +
         (unsigned)i;
-    quad_normals(quad, V.noise_id, philox_schedule(key0, key1), z);
+    quad_normals(quad, V.noise_id, key, z);
   }
 #pragma unroll
   for (int m = 0; m < 4; ++m) {
@@ -134,7 +134,7 @@ aug_status tex_create(const aug_volume_desc* h, int n, void** handle) {
 
 aug_status tex_warp_fwd(void* handle, uint64_t seed, cudaStream_t st) {
   TexSet* S = (TexSet*)handle;
-  const unsigned k0 = (unsigned)seed, k1 = (unsigned)(seed >> 32);
+  const PhiloxKey key = philox_schedule((unsigned)seed, (unsigned)(seed >> 32));
   for (const TexEntry& e : S->v) {
     const aug_volume_desc& d = e.d;
     if (d.out_image == nullptr && d.out_label == nullptr) continue;
@@ -156,7 +156,7 @@ aug_status tex_warp_fwd(void* handle, uint64_t seed, cudaStream_t st) {
     V.sigma = d.noise_sigma;
     V.noise_id = d.noise_id;
     const dim3 grid((d.out_nx + 31) / 32, (d.out_ny + kTexNW - 1) / kTexNW, (d.out_nz + 3) / 4);
-    k_tex_fwd<<<grid, kTexNW * 32, 0, st>>>(V, k0, k1);
+    k_tex_fwd<<<grid, kTexNW * 32, 0, st>>>(V, key);
     if (cudaGetLastError() != cudaSuccess) return AUG_ERR_CUDA;
   }
   return AUG_OK;
