@@ -69,6 +69,8 @@ __global__ void k_prepare(const aug_volume_desc* __restrict__ descs, int n_vols,
                           int need_label, unsigned forbid_flags, VolConst* __restrict__ tab,
                           WsHeader* ws) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
+  // The main kernel that follows starts its dynamic tile schedule at 0.
+  if (v == 0 && ws != nullptr) ws->tile_next = 0ull;
   if (v >= n_vols) return;
   const aug_volume_desc d = descs[v];
   bool ok = desc_valid(d, needs_image(d, need), f32_only != 0);

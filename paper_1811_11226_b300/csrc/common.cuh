@@ -23,7 +23,8 @@ constexpr int MAX_DIM = 8192;
 struct WsHeader {
   int status;      // first device-side error (aug_status), 0 if none
   int bad_volume;  // volume index of that error
-  int pad[62];
+  unsigned long long tile_next;  // dynamic tile counter (zeroed by the prologue)
+  int pad[60];
 };
 static_assert(sizeof(WsHeader) == 256, "header size");
 

@@ -2,10 +2,11 @@
 // image sample, nearest label sample, intensity affine, Philox noise.
 //
 //  * k_fwd_batched: ONE persistent launch for a whole batch of unequal
-//    volumes.  Every CTA walks the concatenated tile list of all volumes
-//    (static round-robin: CTA b takes global tiles b, b+G, ...), so CTAs that
-//    run at the same time work on neighbouring tiles of the same volume and
-//    the input they gather from stays in L2.
+//    volumes.  The CTAs take the tiles of the concatenated tile list of all
+//    volumes in order, each claiming the next unclaimed tile when it finishes
+//    one, so CTAs that run at the same time work on neighbouring tiles of the
+//    same volume (the input they gather from stays in L2) and all of them
+//    finish together.
 //  * k_fwd_volume: the plain form -- one launch per volume, one CTA per tile,
 //    descriptor passed by value.
 //
@@ -338,19 +339,20 @@ __device__ __forceinline__ void fwd_tile(const VolConst& vc, int t, const Philox
 }
 
 // MB: minimum resident CTAs per SM requested from the register allocator
-// (1 = no constraint); part of the variant, chosen by measurement.
+// (1 = no constraint); part of the variant, chosen by measurement.  Tiles are
+// handed out dynamically (counter = the workspace's tile counter, zeroed by
+// the prologue), which keeps every SM busy until the last tiles.
 template <int NW, int QZ, int MB, int PD>
 __global__ void __launch_bounds__(NW * 32, MB)
     k_fwd_batched(const aug_volume_desc* __restrict__ descs, int n_vols,
-                  const VolConst* __restrict__ tab, const PhiloxKey key) {
+                  const VolConst* __restrict__ tab, const PhiloxKey key,
+                  unsigned long long* counter) {
   __shared__ SchedSmem<NW * 32> sm;
-  for_each_tile<NW, QZ, true>(
-      descs, n_vols, sm, [](int, int) {},
-      [&](int v, int t, long long) {
-        const VolConst& vc = tab[v];
-        if (vc.ok && (vc.out_image != nullptr || vc.out_label != nullptr))
-          fwd_tile<NW, QZ, PD>(vc, t, key);
-      });
+  for_each_tile_dynamic<NW, QZ, true>(descs, n_vols, sm, counter, [&](int v, int t, long long) {
+    const VolConst& vc = tab[v];
+    if (vc.ok && (vc.out_image != nullptr || vc.out_label != nullptr))
+      fwd_tile<NW, QZ, PD>(vc, t, key);
+  });
 }
 
 template <int NW, int QZ, int MB, int PD>
@@ -365,7 +367,8 @@ __global__ void __launch_bounds__(NW * 32, MB)
 
 // ---- host launchers ----------------------------------------------------------
 namespace {
-using FwdBK = void (*)(const aug_volume_desc*, int, const VolConst*, const PhiloxKey);
+using FwdBK = void (*)(const aug_volume_desc*, int, const VolConst*, const PhiloxKey,
+                       unsigned long long*);
 using FwdVK = void (*)(const aug_volume_desc, const PhiloxKey);
 struct FwdVariant {
   int nw, qz;
@@ -392,13 +395,14 @@ const char* fwd_variant_name(int v) { return kFwdNames[v]; }
 cudaError_t launch_fwd_batched(int variant, const aug_volume_desc* d, int n, unsigned k0,
                                unsigned k1, VolConst* tab, WsHeader* ws, cudaStream_t st) {
   const FwdVariant& fv = kFwd[variant];
+  if (ws == nullptr) return cudaErrorInvalidValue;
   const int block = fv.nw * 32;
   const int grid = persistent_grid((const void*)fv.batched, block, 0);
   if (grid <= 0) return cudaErrorInvalidConfiguration;
   cudaError_t e = launch_prepare(d, n, NEED_IMAGE_IF_OUT, false, nullptr, nullptr, false, tab, ws,
                                  st);
   if (e != cudaSuccess) return e;
-  fv.batched<<<grid, block, 0, st>>>(d, n, tab, philox_schedule(k0, k1));
+  fv.batched<<<grid, block, 0, st>>>(d, n, tab, philox_schedule(k0, k1), &ws->tile_next);
   return cudaGetLastError();
 }
 

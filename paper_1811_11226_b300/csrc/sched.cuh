@@ -3,7 +3,8 @@
 // The global work list is the concatenation, in batch order, of every
 // volume's output tiles.  CTA b of a grid of G takes global tiles b, b+G,
 // b+2G, ... (static round-robin, so CTAs running at the same time work on
-// neighbouring tiles of the same volume and its input stays in L2).
+// neighbouring tiles of the same volume and its input stays in L2), or, in
+// the dynamic form, the next unclaimed tile of that list.
 //
 // Volumes are processed in chunks of BLOCK (one volume per thread): each
 // thread reads the output dimensions of one descriptor, and a block-wide scan
@@ -26,6 +27,7 @@ struct SchedSmem {
   long long vox_pre[BLOCK + 1];   // exclusive prefix of output voxels within the chunk
   int warp_tiles[BLOCK / 32];
   long long warp_vox[BLOCK / 32];
+  long long next;                 // dynamic schedule: the CTA's current global tile
 };
 
 // Output dims of a descriptor if they are valid, else 0 tiles / 0 voxels (the
@@ -43,6 +45,49 @@ __device__ __forceinline__ void volume_counts(const aug_volume_desc* d, int& til
   vox = ok ? (long long)onx * ony * onz : 0;
 }
 
+// Per-volume tile and voxel prefix sums of the chunk of cnt volumes starting
+// at c0, into sm.tile_pre / sm.vox_pre (all threads of the CTA together; the
+// leading barrier protects the previous chunk's readers).
+template <int NW, int QZ, bool FLAT>
+__device__ __forceinline__ void chunk_scan(const aug_volume_desc* __restrict__ descs, int c0,
+                                           int cnt, SchedSmem<NW * 32>& sm) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int t = 0;
+  long long x = 0;
+  if ((int)threadIdx.x < cnt) volume_counts<NW, QZ, FLAT>(descs + c0 + threadIdx.x, t, x);
+  // Inclusive warp scan, then across warps.
+  int ti = t;
+  long long xi = x;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int a = __shfl_up_sync(FULL_MASK, ti, o);
+    const long long b = __shfl_up_sync(FULL_MASK, xi, o);
+    if (lane >= o) {
+      ti += a;
+      xi += b;
+    }
+  }
+  __syncthreads();
+  if (lane == 31) {
+    sm.warp_tiles[warp] = ti;
+    sm.warp_vox[warp] = xi;
+  }
+  __syncthreads();
+  int wt = 0;
+  long long wx = 0;
+  for (int w = 0; w < warp; ++w) {
+    wt += sm.warp_tiles[w];
+    wx += sm.warp_vox[w];
+  }
+  sm.tile_pre[threadIdx.x + 1] = wt + ti;
+  sm.vox_pre[threadIdx.x + 1] = wx + xi;
+  if (threadIdx.x == 0) {
+    sm.tile_pre[0] = 0;
+    sm.vox_pre[0] = 0;
+  }
+  __syncthreads();
+}
+
 // Calls body(v, local_tile, vox_offset) for every tile of this CTA, in
 // increasing global order, with all threads of the CTA together (body may
 // synchronise).  chunk_begin(c0, cnt) runs once per chunk before its tiles
@@ -52,46 +97,12 @@ __device__ __forceinline__ void for_each_tile(const aug_volume_desc* __restrict_
                                               int n_vols, SchedSmem<NW * 32>& sm,
                                               ChunkF&& chunk_begin, BodyF&& body) {
   constexpr int BLOCK = NW * 32;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long long G = gridDim.x;
   long long gbase = 0;    // global index of the chunk's first tile
   long long voxbase = 0;  // output voxels before the chunk
   for (int c0 = 0; c0 < n_vols; c0 += BLOCK) {
     const int cnt = min(BLOCK, n_vols - c0);
-    int t = 0;
-    long long x = 0;
-    if ((int)threadIdx.x < cnt) volume_counts<NW, QZ, FLAT>(descs + c0 + threadIdx.x, t, x);
-    // Inclusive warp scan, then across warps.
-    int ti = t;
-    long long xi = x;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const int a = __shfl_up_sync(FULL_MASK, ti, o);
-      const long long b = __shfl_up_sync(FULL_MASK, xi, o);
-      if (lane >= o) {
-        ti += a;
-        xi += b;
-      }
-    }
-    __syncthreads();  // previous chunk's readers are done with sm
-    if (lane == 31) {
-      sm.warp_tiles[warp] = ti;
-      sm.warp_vox[warp] = xi;
-    }
-    __syncthreads();
-    int wt = 0;
-    long long wx = 0;
-    for (int w = 0; w < warp; ++w) {
-      wt += sm.warp_tiles[w];
-      wx += sm.warp_vox[w];
-    }
-    sm.tile_pre[threadIdx.x + 1] = wt + ti;
-    sm.vox_pre[threadIdx.x + 1] = wx + xi;
-    if (threadIdx.x == 0) {
-      sm.tile_pre[0] = 0;
-      sm.vox_pre[0] = 0;
-    }
-    __syncthreads();
+    chunk_scan<NW, QZ, FLAT>(descs, c0, cnt, sm);
     chunk_begin(c0, cnt);
     const int chunk_tiles = sm.tile_pre[cnt];
     int vi = 0;
@@ -103,6 +114,49 @@ __device__ __forceinline__ void for_each_tile(const aug_volume_desc* __restrict_
     }
     gbase += chunk_tiles;
     voxbase += sm.vox_pre[cnt];
+  }
+}
+
+// Dynamic form of for_each_tile (same global tile order, same body
+// arguments): a CTA takes the next unclaimed global tile from *counter (zero
+// at launch) whenever it finishes one, so CTAs that drew cheap tiles take more
+// of them and all finish within about one tile of each other.  The index of
+// the following tile is claimed while the current one is processed (its
+// latency is hidden), and CTAs claim tiles in increasing order, so the tiles
+// in flight at any time are neighbours, as in the static order.  body must not
+// synchronise the CTA.
+template <int NW, int QZ, bool FLAT, typename BodyF>
+__device__ __forceinline__ void for_each_tile_dynamic(const aug_volume_desc* __restrict__ descs,
+                                                      int n_vols, SchedSmem<NW * 32>& sm,
+                                                      unsigned long long* counter,
+                                                      BodyF&& body) {
+  constexpr int BLOCK = NW * 32;
+  if (threadIdx.x == 0) sm.next = (long long)atomicAdd(counter, 1ull);
+  __syncthreads();
+  long long g = sm.next;  // same value in every thread: the loops below are uniform
+  int c0 = -BLOCK, cnt = 0, vi = 0;
+  long long gbase = 0, gend = 0, voxbase = 0, chunk_vox = 0;
+  while (true) {
+    while (g >= gend) {
+      c0 += BLOCK;
+      if (c0 >= n_vols) return;
+      cnt = min(BLOCK, n_vols - c0);
+      gbase = gend;
+      voxbase += chunk_vox;
+      chunk_scan<NW, QZ, FLAT>(descs, c0, cnt, sm);
+      gend = gbase + sm.tile_pre[cnt];
+      chunk_vox = sm.vox_pre[cnt];
+      vi = 0;
+    }
+    unsigned long long claimed = 0ull;
+    if (threadIdx.x == 0) claimed = atomicAdd(counter, 1ull);
+    const int lt = (int)(g - gbase);
+    while (sm.tile_pre[vi + 1] <= lt) ++vi;
+    body(c0 + vi, lt - sm.tile_pre[vi], voxbase + sm.vox_pre[vi]);
+    __syncthreads();  // every thread has read sm.next for this tile
+    if (threadIdx.x == 0) sm.next = (long long)claimed;
+    __syncthreads();
+    g = sm.next;
   }
 }
 
