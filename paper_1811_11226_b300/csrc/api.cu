@@ -67,10 +67,10 @@ int persistent_grid(const void* kernel, int block, size_t smem) {
 __global__ void k_prepare(const aug_volume_desc* __restrict__ descs, int n_vols, int need,
                           int f32_only, const float* const* gout, float* const* gin,
                           int need_label, unsigned forbid_flags, VolConst* __restrict__ tab,
-                          WsHeader* ws) {
+                          WsHeader* ws, unsigned long long tile_next0) {
   const int v = blockIdx.x * blockDim.x + threadIdx.x;
-  // The main kernel that follows starts its dynamic tile schedule at 0.
-  if (v == 0 && ws != nullptr) ws->tile_next = 0ull;
+  // First tile index that the dynamic schedule of the next kernel hands out.
+  if (v == 0 && ws != nullptr) ws->tile_next = tile_next0;
   if (v >= n_vols) return;
   const aug_volume_desc d = descs[v];
   bool ok = desc_valid(d, needs_image(d, need), f32_only != 0);
@@ -86,11 +86,12 @@ __global__ void k_prepare(const aug_volume_desc* __restrict__ descs, int n_vols,
 
 cudaError_t launch_prepare(const aug_volume_desc* d, int n, int need, bool f32_only,
                            const float* const* gout, float* const* gin, bool need_label,
-                           VolConst* tab, WsHeader* ws, cudaStream_t st) {
+                           VolConst* tab, WsHeader* ws, cudaStream_t st,
+                           unsigned long long tile_next0) {
   // The adjoint (need == NEED_IMAGE_ALWAYS) has no adjoint of the window clamp.
   const unsigned forbid = need == NEED_IMAGE_ALWAYS ? (unsigned)AUG_FLAG_WINDOW : 0u;
   k_prepare<<<(n + 127) / 128, 128, 0, st>>>(d, n, need, f32_only ? 1 : 0, gout, gin,
-                                              need_label ? 1 : 0, forbid, tab, ws);
+                                              need_label ? 1 : 0, forbid, tab, ws, tile_next0);
   return cudaGetLastError();
 }
 

@@ -340,8 +340,8 @@ __device__ __forceinline__ void fwd_tile(const VolConst& vc, int t, const Philox
 
 // MB: minimum resident CTAs per SM requested from the register allocator
 // (1 = no constraint); part of the variant, chosen by measurement.  Tiles are
-// handed out dynamically (counter = the workspace's tile counter, zeroed by
-// the prologue), which keeps every SM busy until the last tiles.
+// handed out dynamically (counter = the workspace's tile counter, set to the
+// grid size by the prologue), which keeps every SM busy until the last tiles.
 template <int NW, int QZ, int MB, int PD>
 __global__ void __launch_bounds__(NW * 32, MB)
     k_fwd_batched(const aug_volume_desc* __restrict__ descs, int n_vols,
@@ -399,8 +399,10 @@ cudaError_t launch_fwd_batched(int variant, const aug_volume_desc* d, int n, uns
   const int block = fv.nw * 32;
   const int grid = persistent_grid((const void*)fv.batched, block, 0);
   if (grid <= 0) return cudaErrorInvalidConfiguration;
+  // The prologue sets the tile counter to the grid size: CTA b takes tile b
+  // first and claims later tiles from the counter.
   cudaError_t e = launch_prepare(d, n, NEED_IMAGE_IF_OUT, false, nullptr, nullptr, false, tab, ws,
-                                 st);
+                                 st, (unsigned long long)grid);
   if (e != cudaSuccess) return e;
   fv.batched<<<grid, block, 0, st>>>(d, n, tab, philox_schedule(k0, k1), &ws->tile_next);
   return cudaGetLastError();

@@ -20,7 +20,8 @@ const char* fwd_variant_name(int v);
 // Prologue of each batched call (k_prepare): per-volume constant table.
 cudaError_t launch_prepare(const aug_volume_desc* d, int n, int need, bool f32_only,
                            const float* const* gout, float* const* gin, bool need_label,
-                           VolConst* tab, WsHeader* ws, cudaStream_t st);
+                           VolConst* tab, WsHeader* ws, cudaStream_t st,
+                           unsigned long long tile_next0 = 0ull);
 
 cudaError_t launch_fwd_batched(int variant, const aug_volume_desc* d, int n, unsigned k0,
                                unsigned k1, VolConst* tab, WsHeader* ws, cudaStream_t st);

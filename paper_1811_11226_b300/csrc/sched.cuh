@@ -118,20 +118,21 @@ __device__ __forceinline__ void for_each_tile(const aug_volume_desc* __restrict_
 }
 
 // Dynamic form of for_each_tile (same global tile order, same body
-// arguments): a CTA takes the next unclaimed global tile from *counter (zero
-// at launch) whenever it finishes one, so CTAs that drew cheap tiles take more
-// of them and all finish within about one tile of each other.  The index of
-// the following tile is claimed while the current one is processed (its
-// latency is hidden), and CTAs claim tiles in increasing order, so the tiles
-// in flight at any time are neighbours, as in the static order.  body must not
-// synchronise the CTA.
+// arguments): CTA b of G starts with global tile b, and whenever it finishes
+// a tile takes the next unclaimed one, (*counter)++ (*counter is G at launch),
+// so CTAs that drew cheap tiles take more of them and all finish
+// within about one tile of each other.  The index of the following tile is
+// claimed while the current one is processed (its latency is hidden), and
+// tiles are claimed in increasing order, so the tiles in flight at any time
+// are neighbours, as in the static order.  A CTA without a first tile exits
+// without touching the counter.  body must not synchronise the CTA.
 template <int NW, int QZ, bool FLAT, typename BodyF>
 __device__ __forceinline__ void for_each_tile_dynamic(const aug_volume_desc* __restrict__ descs,
                                                       int n_vols, SchedSmem<NW * 32>& sm,
                                                       unsigned long long* counter,
                                                       BodyF&& body) {
   constexpr int BLOCK = NW * 32;
-  if (threadIdx.x == 0) sm.next = (long long)atomicAdd(counter, 1ull);
+  if (threadIdx.x == 0) sm.next = blockIdx.x;
   __syncthreads();
   long long g = sm.next;  // same value in every thread: the loops below are uniform
   int c0 = -BLOCK, cnt = 0, vi = 0;
@@ -148,13 +149,13 @@ __device__ __forceinline__ void for_each_tile_dynamic(const aug_volume_desc* __r
       chunk_vox = sm.vox_pre[cnt];
       vi = 0;
     }
-    unsigned long long claimed = 0ull;
-    if (threadIdx.x == 0) claimed = atomicAdd(counter, 1ull);
+    long long claimed = 0;
+    if (threadIdx.x == 0) claimed = (long long)atomicAdd(counter, 1ull);
     const int lt = (int)(g - gbase);
     while (sm.tile_pre[vi + 1] <= lt) ++vi;
     body(c0 + vi, lt - sm.tile_pre[vi], voxbase + sm.vox_pre[vi]);
-    __syncthreads();  // every thread has read sm.next for this tile
-    if (threadIdx.x == 0) sm.next = (long long)claimed;
+    __syncthreads();  // every thread is done with sm for this tile
+    if (threadIdx.x == 0) sm.next = claimed;
     __syncthreads();
     g = sm.next;
   }
@@ -176,6 +177,6 @@ __device__ __forceinline__ bool needs_image(const aug_volume_desc& d, int need) 
 __global__ void k_prepare(const aug_volume_desc* __restrict__ descs, int n_vols, int need,
                           int f32_only, const float* const* gout, float* const* gin,
                           int need_label, unsigned forbid_flags, VolConst* __restrict__ tab,
-                          WsHeader* ws);
+                          WsHeader* ws, unsigned long long tile_next0);
 
 }  // namespace augk
