@@ -273,8 +273,8 @@ def run_ours(args, rank, world, local):
     if args.only in ("all", "fwd"):
         # ---- headline: batched forward, 64 uneven volumes ----------------------------------
         w1 = workloads.config1(device=dev)
-        for v in w1.vols:
-            v.noise_id += 64 * rank
+        for v, nid in zip(w1.vols, D.replica_noise_ids(len(w1.vols), rank)):
+            v.noise_id = nid
         batch, (img_all, lab_all), (oi_all, ol_all) = build_fwd(w1, A)
         ws = A.make_workspace(batch.n, 6, dev)
         n_out = sum(batch.out_voxels())

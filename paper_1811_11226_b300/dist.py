@@ -50,6 +50,13 @@ def reduce_sum(value: float, device="cpu") -> float:
     return float(t.item())
 
 
+def replica_noise_ids(n_local: int, rank: int):
+    """Philox volume words (descriptor noise_id) of the n_local volumes of one
+    replica: rank r takes r * n_local .. r * n_local + n_local - 1, so no two
+    volumes of a multi-GPU job draw the same noise stream."""
+    return [rank * n_local + b for b in range(n_local)]
+
+
 def partition(weights: Sequence[int], world: int, rank: int):
     """Indices of the volumes rank `rank` of `world` takes: contiguous ranges
     with (nearly) equal total weight (e.g. output voxels).  Every index goes to
