@@ -31,8 +31,11 @@
  *     (k = 4m..4m+3) -- see aug_warp_fwd.  Optional per volume (aug_flags):
  *     occlusion of a z-slab of the output and a window/level clamp.
  *   - All pointers are DEVICE pointers unless stated otherwise.  The caller
- *     owns every buffer; the library allocates no device memory in any entry
- *     point.  Every entry point only enqueues work on `stream` and returns
+ *     owns every buffer.  Two entry points allocate device memory, as their
+ *     declarations state: aug_warp_fwd_host (staging slots from the
+ *     stream-ordered pool, returned at the end of the call) and
+ *     aug_tex_create (the CUDA arrays its handle owns); no other entry point
+ *     allocates.  Every entry point only enqueues work on `stream` and returns
  *     without synchronising, except aug_read_device_status and aug_autotune.
  *   - Argument errors found on the host are returned synchronously; errors
  *     found in device descriptors are written to the workspace status word
@@ -385,11 +388,14 @@ aug_status seg_loss_fwd_bwd(const aug_volume_desc* d_descs, int n_vols, const fl
  * Limits: 1 <= n_vols <= 64 (else AUG_ERR_INVALID_ARG), 1 <= n_classes <= 8
  * (else AUG_ERR_UNSUPPORTED); at most 256 thread blocks per pass.
  * d_status: NULL, or a device int32[2] that receives (status, bad volume) of
- * this call's descriptor checks (0, 0 when every descriptor is valid).
+ * this call's descriptor checks: (0, -1) when every descriptor is valid, else
+ * (AUG_ERR_DESCRIPTOR, index of the first invalid volume), as
+ * aug_read_device_status reports them.  d_grad_p NULL computes the loss only.
  *
- * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  All calls share the one array and each call overwrites it, so
+ * The first call on a device (and again after the device's context has been
+ * recreated, e.g. by cudaDeviceReset) looks up the array's device address in
+ * the current context, with that device current; make that first call before
+ * any stream capture.  All calls share the one array and each call overwrites it, so
  * calls that may overlap on the GPU (different streams, or several host
  * threads) race and give wrong results: serialise them. */
 aug_status iou_loss_fwd_bwd_noalloc(const aug_volume_desc* d_descs, int n_vols,

@@ -1,7 +1,10 @@
 // Overlap losses of Sec. 5.C: launcher, finalize table and the plain-probability
 // pass kernels (the kernels themselves are in iou.cuh).
+#include <cuda.h>
+
 #include <map>
 #include <mutex>
+#include <utility>
 
 #include "iou.cuh"
 
@@ -33,13 +36,14 @@ const char* iou_variant_name(int v) { return kIouNames[v]; }
 cudaError_t launch_iou(int variant, const aug_volume_desc* d, int n, const float* p, int C,
                        int kind, float power, bool logits, float* loss, float* gp,
                        VolConst* tab, double* partials, float2* coefs, WsHeader* ws,
-                       cudaStream_t st) {
+                       cudaStream_t st, int max_grid) {
   const int xf = (power != 1.0f ? XF_POW : 0) | (logits ? XF_LOGITS : 0);
   const IouPasses& iv = passes_for(variant, xf);
   const int block = iv.nw * 32;
   const IouPassK ks = iv.sums[C - 1];
-  const int grid = persistent_grid((const void*)ks, block, 0);
+  int grid = persistent_grid((const void*)ks, block, 0);
   if (grid <= 0) return cudaErrorInvalidConfiguration;
+  if (max_grid > 0 && grid > max_grid) grid = max_grid;
   cudaError_t e = launch_prepare(d, n, NEED_IMAGE_NEVER, false, nullptr, nullptr, true, tab, ws,
                                  st);
   if (e != cudaSuccess) return e;
@@ -49,8 +53,9 @@ cudaError_t launch_iou(int variant, const aug_volume_desc* d, int n, const float
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   if (gp) {
     const IouPassK kg = iv.grad[C - 1];
-    const int g2 = persistent_grid((const void*)kg, block, 0);
+    int g2 = persistent_grid((const void*)kg, block, 0);
     if (g2 <= 0) return cudaErrorInvalidConfiguration;
+    if (max_grid > 0 && g2 > max_grid) g2 = max_grid;
     kg<<<g2, block, 0, st>>>(d, n, tab, p, gp, coefs, nullptr, power);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
@@ -80,17 +85,59 @@ constexpr size_t kStaticScratchBytes =
 // Every device that loads the library holds this array until the process exits.
 static __device__ __align__(256) unsigned char g_iou_scratch[kStaticScratchBytes];
 
-std::mutex g_scratch_mu;
-std::map<int, void*> g_scratch_ptr;  // device -> device address of g_iou_scratch
+// Driver calls for the identity of the current context, fetched through the
+// runtime (no link-time dependency on the driver library).
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
 
-// Device address of the scratch array on the current device, looked up once per
-// device (the host-side symbol is only a stand-in, never a device pointer).
+std::mutex g_scratch_mu;
+// (device, context id) -> device address of g_iou_scratch in that context.
+std::map<std::pair<int, unsigned long long>, void*> g_scratch_ptr;
+
+// Identity of the current context: unique within the process, so a context
+// created after cudaDeviceReset (whose module copy of the array may sit at
+// another address) never matches an address looked up in an earlier one.
+cudaError_t current_context_id(unsigned long long* id) {
+  static std::once_flag once;
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  std::call_once(once, [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = (CtxGetCurrentFn)p;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = (CtxGetIdFn)p;
+  });
+  if (get_current == nullptr || get_id == nullptr) return cudaErrorNotSupported;
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS) return cudaErrorDeviceUninitialized;
+  if (ctx == nullptr) {
+    // No runtime call has made the device's context current on this thread
+    // yet: cudaFree(NULL) does (and is otherwise a no-op).
+    const cudaError_t e = cudaFree(nullptr);
+    if (e != cudaSuccess) return e;
+    if (get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr) return cudaErrorDeviceUninitialized;
+  }
+  return get_id(ctx, id) == CUDA_SUCCESS ? cudaSuccess : cudaErrorDeviceUninitialized;
+}
+
+// Device address of the scratch array in the current context.  The host-side
+// symbol is only a stand-in, never a device pointer, so the address is looked
+// up with cudaGetSymbolAddress, once per device and context.
 cudaError_t scratch_address(void** out) {
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
+  unsigned long long ctx = 0;
+  if ((e = current_context_id(&ctx)) != cudaSuccess) return e;
   std::lock_guard<std::mutex> lk(g_scratch_mu);
-  auto it = g_scratch_ptr.find(dev);
+  const auto key = std::make_pair(dev, ctx);
+  auto it = g_scratch_ptr.find(key);
   if (it != g_scratch_ptr.end()) {
     *out = it->second;
     return cudaSuccess;
@@ -98,7 +145,7 @@ cudaError_t scratch_address(void** out) {
   void* p = nullptr;
   e = cudaGetSymbolAddress(&p, g_iou_scratch);
   if (e != cudaSuccess) return e;
-  g_scratch_ptr[dev] = p;
+  g_scratch_ptr[key] = p;
   *out = p;
   return cudaSuccess;
 }
@@ -121,33 +168,20 @@ extern "C" aug_status iou_loss_fwd_bwd_noalloc(const aug_volume_desc* d_descs, i
   VolConst* tab = (VolConst*)((char*)base + sizeof(WsHeader));
   double* partials = (double*)((char*)tab + kStaticTableBytes);
   float2* coefs = (float2*)((char*)partials + kStaticPartialBytes);
-  // The status word keeps the previous call's value: clear it first.
-  if (cudaMemsetAsync(ws, 0, 2 * sizeof(int), st) != cudaSuccess) return AUG_ERR_CUDA;
-
-  const int variant = aug_get_variant(2);
-  const IouPasses& iv = iou_passes<0>(variant < 0 ? 0 : variant);
-  const int block = iv.nw * 32;
-  const int C = n_classes;
-  const IouPassK ks = iv.sums[C - 1];
-  int grid = persistent_grid((const void*)ks, block, 0);
-  if (grid <= 0) return AUG_ERR_CUDA;
-  if (grid > kStaticMaxCtas) grid = kStaticMaxCtas;
-  if (launch_prepare(d_descs, n_vols, NEED_IMAGE_NEVER, false, nullptr, nullptr, true, tab, ws,
-                     st) != cudaSuccess)
+  // The status words keep the previous call's values: status 0, bad volume -1
+  // (the convention of aug_read_device_status when no descriptor is invalid).
+  if (cudaMemsetAsync(&ws->status, 0, sizeof(int), st) != cudaSuccess ||
+      cudaMemsetAsync(&ws->bad_volume, 0xff, sizeof(int), st) != cudaSuccess)
     return AUG_ERR_CUDA;
-  // Every CTA writes all of its partial slots (zero where it has no tile), so
-  // the previous call's partial sums need no clearing.
-  ks<<<grid, block, 0, st>>>(d_descs, n_vols, tab, d_p, nullptr, nullptr, partials, 1.0f);
-  if (cudaGetLastError() != cudaSuccess) return AUG_ERR_CUDA;
-  kIouFin[C - 1]<<<n_vols, 256, 0, st>>>(partials, grid, n_vols, AUG_LOSS_IOU, d_loss,
-                                         d_grad_p ? coefs : nullptr);
-  if (cudaGetLastError() != cudaSuccess) return AUG_ERR_CUDA;
-  if (d_grad_p) {
-    const IouPassK kg = iv.grad[C - 1];
-    const int g2 = grid;  // any grid works for the write pass; keep the same
-    kg<<<g2, block, 0, st>>>(d_descs, n_vols, tab, d_p, d_grad_p, coefs, nullptr, 1.0f);
-    if (cudaGetLastError() != cudaSuccess) return AUG_ERR_CUDA;
-  }
+  // The same launcher as iou_loss_fwd_bwd, with its grids capped to the
+  // partial-sum slots the array holds.  Every CTA of the sums pass writes all
+  // of its partial slots (zero where it has no tile), so the previous call's
+  // partial sums need no clearing.
+  const int variant = aug_get_variant(2);
+  if (launch_iou(variant < 0 ? 0 : variant, d_descs, n_vols, d_p, n_classes, AUG_LOSS_IOU, 1.0f,
+                 false, d_loss, d_grad_p, tab, partials, coefs, ws, st,
+                 kStaticMaxCtas) != cudaSuccess)
+    return AUG_ERR_CUDA;
   if (d_status != nullptr &&
       cudaMemcpyAsync(d_status, ws, 2 * sizeof(int), cudaMemcpyDeviceToDevice, st) !=
           cudaSuccess)

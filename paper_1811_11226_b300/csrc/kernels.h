@@ -37,10 +37,12 @@ cudaError_t launch_bwd(int variant, const aug_volume_desc* d, int n, const float
 int iou_num_variants();
 const char* iou_variant_name(int v);
 // Overlap loss `kind` (aug_loss_kind) on q = (logits ? softmax(p) : p)^power.
+// max_grid > 0 caps the CTAs of both passes (partial-sum slots of a fixed
+// scratch array).
 cudaError_t launch_iou(int variant, const aug_volume_desc* d, int n, const float* p, int C,
                        int kind, float power, bool logits, float* loss, float* gp,
                        VolConst* tab, double* partials, float2* coefs, WsHeader* ws,
-                       cudaStream_t st);
+                       cudaStream_t st, int max_grid = 0);
 
 // Per-volume random parameters into the descriptors (one CTA).
 cudaError_t launch_sample_params(aug_volume_desc* d, int n, const aug_param_spec& sp,

@@ -50,8 +50,8 @@ def test_adjoint_many_volumes_across_scheduler_chunks():
         G.check_grad(gin[b], ri, f"grad_in {b}")
         floor = 1e-7 * G.summand_scale(v, grads[b].cpu().numpy())
         floored += G.check_grad_affine(gaff[b], rt, f"grad_T {b}", floor=floor)
-    print(f"grad_T: {floored} of {len(cases)} volumes had a vanishing gradient and used "
-          "the rounding floor")
+    print(f"grad_T: {floored} of {len(cases)} volumes had a gradient cancelled below the float32 rounding "
+          "scale of its terms and used that floor")
 
 
 def test_iou_many_volumes_across_scheduler_chunks():
