@@ -16,8 +16,13 @@ Also reported on the same line:
   e2e       -- the same step through the C ABI from pinned host buffers
                (H2D of inputs, D2H of outputs inside the timed region);
   cpu_baseline -- the FP64 oracle on a bounded sample, single thread.
-With --all: the fused label-warp + IOU loss on 8 x 120x120x160 and the
-full-resolution int16 training step.
+  iou       -- the fused label warp + IOU loss on 8 x 120x120x160 (Gvox/s);
+  train_step -- the full-resolution int16 training step: 16 volumes of
+               512^2 x 300-600 -> 128x128x160 crops, forward + IOU + affine
+               adjoint in one graph (Gvox/s).
+Each of fwd_bwd, iou and train_step carries its own HBM roofline object.
+With --all: the single small volume, the loss variants, the training step
+from volumes resampled once to 3 mm, and the anti-aliasing Gaussian.
 
 --impl reference times the FP64 oracle (the only reference implementation
 of this method here) on the host cores, on a bounded sample per step.
@@ -62,7 +67,7 @@ def hbm_peak():
 
 # Device sources of the forward kernel (its code and its grid cap): a recorded
 # DRAM-traffic figure is only used while these are unchanged.
-FWD_SOURCES = ("fwd.cu", "common.cuh", "sample.cuh", "sched.cuh")
+FWD_SOURCES = ("fwd.cu", "fwd.cuh", "common.cuh", "sample.cuh", "sched.cuh")
 
 
 def kernel_source_hash():
@@ -459,11 +464,11 @@ def run_ours(args, rank, world, local):
         res["fwd_bwd"] = bench_fwd_bwd(args, A, D, dev, stream, seed, world)
     if args.only == "all" and args.all:
         res["config0"] = bench_config0(args, A, dev, stream, seed)
-    if (args.only == "all" and args.all) or args.only == "iou":
+    if args.only in ("all", "iou"):
         res["iou"] = bench_iou(args, A, dev, stream)
     if (args.only == "all" and args.all) or args.only == "loss":
         res["loss_variants"] = bench_loss_variants(args, A, dev, stream)
-    if (args.only == "all" and args.all) or args.only == "train":
+    if args.only in ("all", "train"):
         res["train_step"] = bench_train(args, A, dev, stream, seed)
     if (args.only == "all" and args.all) or args.only == "train":
         res["train_step_resampled"] = bench_train_resampled(args, A, dev, stream, seed)
@@ -510,6 +515,8 @@ def bench_fwd_bwd(args, A, D, dev, stream, seed, world):
     return {"value": round(world * n_out / (ms_max * 1e-3) / 1e9, 3), "unit": "Gvox/s",
             "ms_per_step": round(ms_max, 4), "workload": "8 x 128^3 f32, fwd + grad_in + grad_T",
             "alg_GBps": round(alg / (ms * 1e-3) / 1e9, 1),
+            "roofline": sub_roofline(alg, ms, "forward + adjoint step (prologue, forward, "
+                                     "zeroing, adjoint, finalize)"),
             "variant": A.aug_variant_name(A.OP_BWD, A.aug_get_variant(A.OP_BWD))}
 
 
@@ -554,6 +561,9 @@ def bench_iou(args, A, dev, stream):
     log(f"[iou] {ms:.4f} ms/step")
     return {"value": round(n_out / (ms * 1e-3) / 1e9, 3), "unit": "Gvox/s",
             "ms_per_step": round(ms, 4), "alg_GBps": round(alg / (ms * 1e-3) / 1e9, 1),
+            "roofline": sub_roofline(alg, ms, "fused label warp + IOU step (prologue, sums "
+                                     "pass, finalize, gradient pass)"),
+            "alg_bytes": "p read 24 B + grad_p written 24 B per output voxel + distinct labels",
             "workload": "8 x 120x120x160 label warp + IOU fwd/bwd, 6 classes"}
 
 
@@ -622,6 +632,8 @@ def bench_train(args, A, dev, stream, seed):
     log(f"[train] {ms:.4f} ms/step")
     return {"value": round(n_out / (ms * 1e-3) / 1e9, 3), "unit": "Gvox/s",
             "ms_per_step": round(ms, 4), "alg_GBps": round(alg / (ms * 1e-3) / 1e9, 1),
+            "roofline": sub_roofline(alg, ms, "training step (forward, IOU fwd/bwd, affine "
+                                     "adjoint) in one graph"),
             "workload": f"{len(vols)} int16 512^2 x 300-600 -> 128x128x160: fwd + IOU fwd/bwd + "
                         "grad_T"}
 
@@ -805,7 +817,15 @@ def main():
                     help="volumes of the training-step workload (profiling runs use fewer)")
     ap.add_argument("--smooth-vols", type=int, default=16,
                     help="volumes of the smoothing workload (profiling runs use fewer)")
+    ap.add_argument("--summarize-ncu", metavar="CSV",
+                    help="print the per-kernel summary of an ncu --csv log (and, with "
+                         "--kernel, the record lines of profiles/*.md) and exit")
+    ap.add_argument("--kernel", help="kernel-name regex for --summarize-ncu")
+    ap.add_argument("--record-variant", help="variant name the --summarize-ncu capture ran")
     args = ap.parse_args()
+    if args.summarize_ncu:
+        summarize_ncu(args.summarize_ncu, args.kernel, variant=args.record_variant)
+        return
     args.warmup = max(3, args.warmup)
 
     from paper_1811_11226_b300 import dist as D
@@ -855,7 +875,12 @@ def main():
                      "peak_kind": peak_kind_note(res["peak_kind"]),
                      "frac_of_nominal_7700": round(res["achieved"] / 7700.0, 4),
                      "traffic": traffic, "alg_bytes_per_launch": res["alg"],
-                     "kernel": "k_fwd_batched"},
+                     "traffic_source": None if traffic is None else (
+                         "profiles/fwd_batched_config1.md: dram__bytes_read.sum + "
+                         "dram__bytes_write.sum of one ncu capture of this kernel variant, "
+                         "record lines printed by bench.py --summarize-ncu from that capture's "
+                         f"CSV (csrc_hash {kernel_source_hash()})"),
+                     "kernel": res.get("kernel", "k_fwd_batched")},
         # The forward is limited by instruction issue, not DRAM: its recorded
         # warp instructions per launch over the measured launch time, against
         # 4 schedulers x SMs x the SM clock sampled during the timed region.
@@ -874,6 +899,66 @@ def main():
         if key in res:
             line[key] = res[key]
     print(json.dumps(line), flush=True)
+
+
+def sub_roofline(alg_bytes, ms, what):
+    """HBM roofline of a whole step: algorithmic bytes / step time against the
+    measured copy peak (the step's kernels together, one graph replay)."""
+    peak, kind = hbm_peak()
+    achieved = alg_bytes / (ms * 1e-3) / 1e9
+    return {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+            "frac": round(achieved / peak, 4), "peak_kind": peak_kind_note(kind),
+            "alg_bytes_per_step": int(alg_bytes), "over": what}
+
+
+def summarize_ncu(path, kernel_regex=None, variant=None):
+    """Summary of an ncu --csv log (one row per kernel launch and metric):
+    per kernel its launches, total and mean gpu__time_duration, and the mean
+    per launch of every other metric, plus the record lines that
+    profile_record() reads (for the kernel matching kernel_regex)."""
+    import csv
+    import re
+    rows = [r for r in csv.reader(open(path)) if len(r) > 10]
+    hdr = rows[0]
+    col = {h: i for i, h in enumerate(hdr)}
+    per = {}
+    for r in rows[1:]:
+        if r[col["ID"]] == "ID":
+            continue
+        name = r[col["Kernel Name"]]
+        met, unit = r[col["Metric Name"]], r[col["Metric Unit"]]
+        val = float(r[col["Metric Value"]].replace(",", ""))
+        scale = {"ns": 1e-6, "us": 1e-3, "usecond": 1e-3, "msecond": 1.0, "ms": 1.0,
+                 "nsecond": 1e-6, "byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9}
+        val *= scale.get(unit, 1.0)
+        d = per.setdefault(name, {}).setdefault(met, [])
+        d.append(val)
+    total_t = sum(sum(m.get("gpu__time_duration.sum", [0.0])) for m in per.values())
+    out = []
+    for name, m in sorted(per.items(), key=lambda kv: -sum(kv[1].get("gpu__time_duration.sum",
+                                                                      [0.0]))):
+        t = m.get("gpu__time_duration.sum", [])
+        line = f"{name[:60]:60s} launches {len(t):5d}  total {sum(t):9.3f} ms  " \
+               f"mean {1e3 * sum(t) / max(len(t), 1):9.1f} us  share {sum(t) / total_t:6.1%}" \
+            if t else name
+        for met, v in m.items():
+            if met != "gpu__time_duration.sum":
+                line += f"  {met} {sum(v) / len(v):.6g}"
+        out.append(line)
+    print("\n".join(out))
+    if kernel_regex:
+        hits = [m for n, m in per.items() if re.search(kernel_regex, n)]
+        if len(hits) == 1:
+            m = hits[0]
+            rd, wr = m.get("dram__bytes_read.sum"), m.get("dram__bytes_write.sum")
+            if rd and wr:
+                print(f"- dram_bytes_per_launch: {int(round(sum(rd) / len(rd) + sum(wr) / len(wr)))}")
+            if m.get("smsp__inst_executed.sum"):
+                v = m["smsp__inst_executed.sum"]
+                print(f"- warp_inst_per_launch: {int(round(sum(v) / len(v)))}")
+            if variant:
+                print(f"- variant: {variant}")
+            print(f"- csrc_hash: {kernel_source_hash()}")
 
 
 def issue_roofline(res):

@@ -68,7 +68,8 @@ typedef enum {
   AUG_ERR_CUDA = 2,        /* a CUDA runtime call or kernel launch failed       */
   AUG_ERR_WORKSPACE = 3,   /* workspace NULL, misaligned or too small           */
   AUG_ERR_DESCRIPTOR = 4,  /* (device status) a volume descriptor is invalid    */
-  AUG_ERR_UNSUPPORTED = 5  /* valid request outside what this library implements */
+  AUG_ERR_UNSUPPORTED = 5, /* valid request outside what this library implements */
+  AUG_ERR_TIMEOUT = 6      /* (device status) a bounded wait for a copy ran out   */
 } aug_status;
 
 typedef enum { AUG_F32 = 0, AUG_I16 = 1 } aug_dtype;
@@ -343,6 +344,16 @@ aug_status aug_warp_bwd(const aug_volume_desc* d_descs, int n_vols,
 aug_status iou_loss_fwd_bwd(const aug_volume_desc* d_descs, int n_vols, const float* d_p,
                             int n_classes, float* d_loss, float* d_grad_p, void* d_workspace,
                             size_t workspace_bytes, aug_stream_t stream);
+
+/* The scalar training loss of Sec. 5.C, the mean over the batch of the
+ * per-volume losses: *d_mean = (1/n_vols) sum_b d_loss[b], summed in double in a
+ * fixed order (reproducible), rounded to float32.  d_grad_p of
+ * iou_loss_fwd_bwd / seg_loss_fwd_bwd is already the gradient of this mean.
+ * d_loss: [n_vols] float32 device; d_mean: one float32 device.  One small
+ * kernel on `stream`.  AUG_ERR_INVALID_ARG: NULL pointers or n_vols outside
+ * 1..65535. */
+aug_status aug_loss_batch_mean(const float* d_loss, int n_vols, float* d_mean,
+                               aug_stream_t stream);
 
 /* ---- overlap-loss variants (Sec. 5.C) in the same fused kernels --------------
  * Generalises iou_loss_fwd_bwd (which is kind = AUG_LOSS_IOU, power = 1,

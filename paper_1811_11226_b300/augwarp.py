@@ -22,7 +22,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libaugwarp.so")
 
 AUG_OK, AUG_ERR_INVALID_ARG, AUG_ERR_CUDA, AUG_ERR_WORKSPACE, AUG_ERR_DESCRIPTOR, \
-    AUG_ERR_UNSUPPORTED = range(6)
+    AUG_ERR_UNSUPPORTED, AUG_ERR_TIMEOUT = range(7)
 AUG_F32, AUG_I16 = 0, 1
 AUG_FLAG_WINDOW, AUG_FLAG_OCCLUDE = 1, 2
 OP_FWD, OP_BWD, OP_IOU = 0, 1, 2
@@ -88,6 +88,8 @@ def _load():
     L.aug_smooth_status.restype = i32
     L.aug_antialias_sigma.argtypes = [C.c_float, C.c_float]
     L.aug_antialias_sigma.restype = C.c_float
+    L.aug_loss_batch_mean.argtypes = [vp, i32, vp, vp]
+    L.aug_loss_batch_mean.restype = i32
     L.iou_loss_fwd_bwd_noalloc.argtypes = [vp, i32, vp, i32, vp, vp, vp, vp]
     L.iou_loss_fwd_bwd_noalloc.restype = i32
     L.aug_num_variants.argtypes = [i32]
@@ -358,6 +360,15 @@ def aug_smooth(images: Sequence[torch.Tensor], outs: Sequence[torch.Tensor], sig
     _check(_L.aug_smooth(h.ctypes.data_as(C.c_void_p), len(h), _stream(stream)), "aug_smooth")
 
 
+def aug_loss_batch_mean(loss: torch.Tensor, stream=None) -> torch.Tensor:
+    """Mean over the batch of per-volume losses (Sec. 5.C), computed on the
+    device: returns a 0-dim float32 tensor."""
+    out = torch.empty((), dtype=torch.float32, device=loss.device)
+    _check(_L.aug_loss_batch_mean(_ptr(loss), int(loss.numel()), _ptr(out), _stream(stream)),
+           "aug_loss_batch_mean")
+    return out
+
+
 def iou_loss_fwd_bwd_noalloc(d_descs: torch.Tensor, n_vols: int, p: torch.Tensor,
                              n_classes: int, loss: torch.Tensor, grad_p: Optional[torch.Tensor],
                              status: Optional[torch.Tensor] = None, stream=None):
@@ -570,7 +581,7 @@ class IouLoss(torch.autograd.Function):
         gp = torch.empty_like(p) if ctx.needs_input_grad[0] else None
         iou_loss_fwd_bwd(batch.d_descs, B, p, Cn, loss, gp, ws)
         ctx.gp = gp
-        return loss.mean()
+        return aug_loss_batch_mean(loss)
 
     @staticmethod
     def backward(ctx, grad):
@@ -596,7 +607,7 @@ class SegLoss(torch.autograd.Function):
         gx = torch.empty_like(x) if ctx.needs_input_grad[0] else None
         seg_loss_fwd_bwd(batch.d_descs, B, x, Cn, loss, gx, ws, kind, power, logits)
         ctx.gx = gx
-        return loss.mean()
+        return aug_loss_batch_mean(loss)
 
     @staticmethod
     def backward(ctx, grad):

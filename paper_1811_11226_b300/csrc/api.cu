@@ -20,7 +20,7 @@ std::map<std::tuple<int, const void*, int, size_t>, int> g_occ;     // -> CTAs p
 int g_variant[3] = {-1, -1, -1};
 // Defaults: the variants measured fastest on the 64-volume forward batch, the
 // 8 x 128^3 adjoint and the 8 x 120x120x160 loss (6 classes).
-const int kDefaultVariant[3] = {10, 8, 3};
+const int kDefaultVariant[3] = {14, 8, 3};
 
 int current_device() {
   int dev = 0;
@@ -197,6 +197,9 @@ bool host_desc_ok(const aug_volume_desc& d) {
   if (d.out_image != nullptr &&
       (d.image == nullptr || (d.image_dtype != AUG_F32 && d.image_dtype != AUG_I16)))
     return false;
+  if (d.out_image != nullptr &&
+      ((uintptr_t)d.image & (d.image_dtype == AUG_I16 ? 1u : 3u)) != 0u)
+    return false;
   if (d.out_label != nullptr && d.label == nullptr) return false;
   return true;
 }
@@ -347,6 +350,13 @@ aug_status seg_loss_fwd_bwd(const aug_volume_desc* d_descs, int n_vols, const fl
   if (s != AUG_OK) return s;
   return run_iou(variant_of(2), d_descs, n_vols, d_x, n_classes, d_loss, d_grad_x, d_workspace,
                  (cudaStream_t)stream, kind, power, logits != 0);
+}
+
+aug_status aug_loss_batch_mean(const float* d_loss, int n_vols, float* d_mean,
+                               aug_stream_t stream) {
+  if (d_loss == nullptr || d_mean == nullptr || n_vols < 1 || n_vols > kMaxVols)
+    return AUG_ERR_INVALID_ARG;
+  return from_cuda(launch_batch_mean(d_loss, n_vols, d_mean, (cudaStream_t)stream));
 }
 
 aug_status aug_sample_params(aug_volume_desc* d_descs, int n_vols, const aug_param_spec* spec,
@@ -529,6 +539,7 @@ const char* aug_status_string(int status) {
     case AUG_ERR_WORKSPACE: return "workspace missing, misaligned or too small";
     case AUG_ERR_DESCRIPTOR: return "invalid volume descriptor";
     case AUG_ERR_UNSUPPORTED: return "unsupported request";
+    case AUG_ERR_TIMEOUT: return "a bounded device wait for a copy ran out";
     default: return "unknown status";
   }
 }

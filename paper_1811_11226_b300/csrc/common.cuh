@@ -71,6 +71,8 @@ __device__ inline bool desc_valid(const aug_volume_desc& d, bool need_image, boo
   ok &= isfinite(d.occ_z0) && isfinite(d.occ_dz) && d.occ_dz >= 0.0f;
   if (need_image) {
     ok &= d.image != nullptr && (d.image_dtype == AUG_F32 || d.image_dtype == AUG_I16);
+    // element-aligned image (a misaligned pointer would fault on the first load)
+    ok &= ((uintptr_t)d.image & (d.image_dtype == AUG_I16 ? 1u : 3u)) == 0u;
     if (f32_only) ok &= d.image_dtype == AUG_F32;
   }
   ok &= !(d.out_label != nullptr && d.label == nullptr);

@@ -10,339 +10,19 @@
 //  * k_fwd_volume: the plain form -- one launch per volume, one CTA per tile,
 //    descriptor passed by value.
 //
-// Each thread walks its z-run one quad (4 z-consecutive voxels, one Philox
-// call) at a time.  The warp re-classifies every quad (interior / exterior /
-// general, from the quad's first and last coordinates), so only quads that
-// actually straddle the input boundary pay for per-tap checks.
-#include "kernels.h"
-#include "sample.cuh"
-#include "sched.cuh"
+// The per-tile code is in fwd.cuh.  The shared-memory brick kernel and its
+// variants are in fwd_brick.cu; they follow this file's variants in the
+// variant numbering of op 0.
+#include "fwd.cuh"
 
 namespace augk {
-
-// Per-tile copy of the volume constants, held in registers.
-template <typename TIn>
-struct FwdP {
-  const TIn* img;
-  const uint8_t* lab;
-  float* oimg;
-  uint8_t* olab;
-  long long dx, dy, dz;
-  int nx, ny, nz, nxy, plane, fill_label;
-  float a, b, sigma, fill, yfill;  // yfill = a * fill + b
-  int klo, khi;                    // occluded output z indices (empty if klo > khi)
-  bool window;                     // clamp the output to [0, 1] after the noise
-};
-
-// Final value of one output voxel: occluded voxels are exactly 0 (nothing
-// after the warp applies to them); otherwise the optional window clamp.
-// POST = false (a run that meets neither) compiles to nothing.
-template <bool POST, typename TIn>
-__device__ __forceinline__ float finish(const FwdP<TIn>& P, int k, float y) {
-  if (!POST) return y;
-  if (k >= P.klo && k <= P.khi) return 0.0f;
-  return P.window ? __saturatef(y) : y;
-}
-template <bool POST, typename TIn>
-__device__ __forceinline__ bool occluded(const FwdP<TIn>& P, int k) {
-  return POST && k >= P.klo && k <= P.khi;
-}
-
-// Exterior quad: every tap reads the fill value, so the sample is constant;
-// only the noise differs per voxel.  The coordinate advances by n steps at once.
-template <bool POST, typename TIn, bool IMG, bool LAB>
-__device__ __forceinline__ void fwd_quad_exterior(const FwdP<TIn>& P, int& o, int n, bool valid,
-                                                  const float z[4], int kq) {
-#pragma unroll
-  for (int m = 0; m < 4; ++m) {
-    if (m < n) {
-      if (valid) {
-        if (IMG) __stcs(P.oimg + o, finish<POST>(P, kq + m, fmaf(P.sigma, z[m], P.yfill)));
-        if (LAB) st_cs_u8(P.olab + o, P.fill_label);
-      }
-      o += P.plane;
-    }
-  }
-}
-
-// Interior / general quad (n = 1..4 z-consecutive voxels, warp-uniform MODE),
-// software-pipelined in groups of PD voxels: the coordinates are stepped
-// once, every tap and label load of a group is issued before any of its
-// samples is interpolated, and the quad's normals are computed while the
-// first group's loads are in flight.  PD trades registers (occupancy) for
-// memory-level parallelism; it is part of the kernel variant.
-template <bool POST, typename TIn, int MODE, bool IMG, bool LAB, bool FULL, int PD>
-__device__ __forceinline__ void fwd_quad(const FwdP<TIn>& P, long long& sx, long long& sy,
-                                         long long& sz, int& o, int n, bool valid,
-                                         bool noisy, unsigned long long quad, unsigned noise_id,
-                                         const PhiloxKey& key, int kq) {
-  float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll
-  for (int g0 = 0; g0 < 4; g0 += PD) {
-    float tap[PD][8];
-    float w[PD][3];
-    int lab[PD];
-#pragma unroll
-    for (int i = 0; i < PD; ++i) {
-      const int m = g0 + i;
-      lab[i] = P.fill_label;
-#pragma unroll
-      for (int d = 0; d < 8; ++d) tap[i][d] = P.fill;
-      w[i][0] = w[i][1] = w[i][2] = 0.0f;
-      if (FULL || m < n) {
-        const int fx = q40_floor(sx), fy = q40_floor(sy), fz = q40_floor(sz);
-        const int hbx = q40_halfbit(sx), hby = q40_halfbit(sy), hbz = q40_halfbit(sz);
-        // An occluded voxel skips the image fetch (warp-uniform: one k per warp).
-        const bool fetch = !occluded<POST>(P, kq + m);
-        if (IMG) {
-          w[i][0] = q40_frac(sx);
-          w[i][1] = q40_frac(sy);
-          w[i][2] = q40_frac(sz);
-        }
-        if (MODE == MODE_INTERIOR) {
-          const int base = (fz * P.ny + fy) * P.nx + fx;
-          if (IMG && fetch) {
-            const TIn* p = P.img + base;
-            tap[i][0] = ld_val(p);
-            tap[i][1] = ld_val(p + 1);
-            tap[i][2] = ld_val(p + P.nx);
-            tap[i][3] = ld_val(p + P.nx + 1);
-            tap[i][4] = ld_val(p + P.nxy);
-            tap[i][5] = ld_val(p + P.nxy + 1);
-            tap[i][6] = ld_val(p + P.nxy + P.nx);
-            tap[i][7] = ld_val(p + P.nxy + P.nx + 1);
-          }
-          if (LAB) lab[i] = __ldg(P.lab + (base + hbx + hby * P.nx + hbz * P.nxy));
-        } else {
-          if (IMG && fetch) {
-            const bool x0 = (unsigned)fx < (unsigned)P.nx,
-                       x1 = (unsigned)(fx + 1) < (unsigned)P.nx;
-            const bool y0 = (unsigned)fy < (unsigned)P.ny,
-                       y1 = (unsigned)(fy + 1) < (unsigned)P.ny;
-            const bool z0 = (unsigned)fz < (unsigned)P.nz,
-                       z1 = (unsigned)(fz + 1) < (unsigned)P.nz;
-            // Unsigned arithmetic wraps harmlessly far outside; an index is only
-            // dereferenced when its tap lies inside the volume.
-            const unsigned ux = (unsigned)P.nx, uxy = (unsigned)P.nxy;
-            const unsigned b =
-                ((unsigned)fz * (unsigned)P.ny + (unsigned)fy) * ux + (unsigned)fx;
-            if (x0 && y0 && z0) tap[i][0] = ld_val(P.img + b);
-            if (x1 && y0 && z0) tap[i][1] = ld_val(P.img + (b + 1u));
-            if (x0 && y1 && z0) tap[i][2] = ld_val(P.img + (b + ux));
-            if (x1 && y1 && z0) tap[i][3] = ld_val(P.img + (b + ux + 1u));
-            if (x0 && y0 && z1) tap[i][4] = ld_val(P.img + (b + uxy));
-            if (x1 && y0 && z1) tap[i][5] = ld_val(P.img + (b + uxy + 1u));
-            if (x0 && y1 && z1) tap[i][6] = ld_val(P.img + (b + uxy + ux));
-            if (x1 && y1 && z1) tap[i][7] = ld_val(P.img + (b + uxy + ux + 1u));
-          }
-          if (LAB) {
-            const int rx = fx + hbx, ry = fy + hby, rz = fz + hbz;
-            if ((unsigned)rx < (unsigned)P.nx && (unsigned)ry < (unsigned)P.ny &&
-                (unsigned)rz < (unsigned)P.nz)
-              lab[i] = __ldg(P.lab + ((rz * P.ny + ry) * P.nx + rx));
-          }
-        }
-        sx += P.dx;
-        sy += P.dy;
-        sz += P.dz;
-      }
-    }
-    if (g0 == 0 && noisy) quad_normals(quad, noise_id, key, z);
-    if (FULL && IMG && PD >= 2) {
-      // Voxel pairs share packed f32x2 instructions (same rounding as scalar).
-#pragma unroll
-      for (int i = 0; i < PD; i += 2) {
-        const int m = g0 + i;
-        const f32x2 tx = pk2(w[i][0], w[i + 1][0]), ty = pk2(w[i][1], w[i + 1][1]);
-        const f32x2 tz = pk2(w[i][2], w[i + 1][2]);
-        f32x2 v0[8];
-#pragma unroll
-        for (int d = 0; d < 8; ++d) v0[d] = pk2(tap[i][d], tap[i + 1][d]);
-        const f32x2 c00 = fma2(tx, sub2(v0[1], v0[0]), v0[0]);
-        const f32x2 c10 = fma2(tx, sub2(v0[3], v0[2]), v0[2]);
-        const f32x2 c01 = fma2(tx, sub2(v0[5], v0[4]), v0[4]);
-        const f32x2 c11 = fma2(tx, sub2(v0[7], v0[6]), v0[6]);
-        const f32x2 c0 = fma2(ty, sub2(c10, c00), c00);
-        const f32x2 c1 = fma2(ty, sub2(c11, c01), c01);
-        const f32x2 v = fma2(tz, sub2(c1, c0), c0);
-        const f32x2 y = fma2(pk2(P.sigma, P.sigma), pk2(z[m], z[m + 1]),
-                             fma2(pk2(P.a, P.a), v, pk2(P.b, P.b)));
-        float y0, y1;
-        upk2(y, y0, y1);
-        y0 = finish<POST>(P, kq + m, y0);
-        y1 = finish<POST>(P, kq + m + 1, y1);
-        if (valid) {
-          __stcs(P.oimg + o, y0);
-          if (LAB) st_cs_u8(P.olab + o, lab[i]);
-          __stcs(P.oimg + o + P.plane, y1);
-          if (LAB) st_cs_u8(P.olab + o + P.plane, lab[i + 1]);
-        }
-        o += 2 * P.plane;
-      }
-      continue;
-    }
-#pragma unroll
-    for (int i = 0; i < PD; ++i) {
-      const int m = g0 + i;
-      if (FULL || m < n) {
-        if (IMG) {
-          const float tx = w[i][0], ty = w[i][1], tz = w[i][2];
-          const float c00 = fmaf(tx, tap[i][1] - tap[i][0], tap[i][0]);
-          const float c10 = fmaf(tx, tap[i][3] - tap[i][2], tap[i][2]);
-          const float c01 = fmaf(tx, tap[i][5] - tap[i][4], tap[i][4]);
-          const float c11 = fmaf(tx, tap[i][7] - tap[i][6], tap[i][6]);
-          const float c0 = fmaf(ty, c10 - c00, c00);
-          const float c1 = fmaf(ty, c11 - c01, c01);
-          const float v = fmaf(tz, c1 - c0, c0);
-          if (valid)
-            __stcs(P.oimg + o, finish<POST>(P, kq + m, fmaf(P.sigma, z[m], fmaf(P.a, v, P.b))));
-        }
-        if (LAB && valid) st_cs_u8(P.olab + o, lab[i]);
-        o += P.plane;
-      }
-    }
-  }
-}
-
-// Quad-by-quad walk of a z-run: every quad is classified on its own (warp
-// vote), so a run that straddles the input boundary pays per-tap checks only
-// where needed.
-template <bool POST, typename TIn, int QZ, int PD, bool IMG, bool LAB>
-__device__ __forceinline__ void fwd_quads(const FwdP<TIn>& P, const TileCoord& tc, long long sx,
-                                          long long sy, long long sz, int o, bool noisy,
-                                          unsigned onx, unsigned ony, unsigned noise_id,
-                                          const PhiloxKey& key) {
-  const long long ds[3] = {P.dx, P.dy, P.dz};
-#pragma unroll 1
-  for (int q = 0; q < QZ; ++q) {
-    const int kq = tc.k0 + 4 * q;
-    if (kq >= tc.k1) break;
-    const int n = min(4, tc.k1 - kq);
-    const unsigned long long quad =
-        ((unsigned long long)(kq >> 2) * ony + (unsigned)tc.jc) * onx + (unsigned)tc.ic;
-    const long long s[3] = {sx, sy, sz};
-    const int mode = warp_mode(classify_run<true>(s, ds, n - 1, P.nx, P.ny, P.nz));
-    if (mode == MODE_EXTERIOR) {
-      float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-      if (noisy) quad_normals(quad, noise_id, key, z);
-      fwd_quad_exterior<POST, TIn, IMG, LAB>(P, o, n, tc.valid, z, kq);
-      sx += (long long)n * P.dx;
-      sy += (long long)n * P.dy;
-      sz += (long long)n * P.dz;
-    } else if (n == 4) {
-      if (mode == MODE_INTERIOR)
-        fwd_quad<POST, TIn, MODE_INTERIOR, IMG, LAB, true, PD>(
-            P, sx, sy, sz, o, 4, tc.valid, noisy, quad, noise_id, key, kq);
-      else
-        fwd_quad<POST, TIn, MODE_GENERAL, IMG, LAB, true, PD>(
-            P, sx, sy, sz, o, 4, tc.valid, noisy, quad, noise_id, key, kq);
-    } else {
-      fwd_quad<POST, TIn, MODE_GENERAL, IMG, LAB, false, PD>(
-          P, sx, sy, sz, o, n, tc.valid, noisy, quad, noise_id, key, kq);
-    }
-  }
-}
-
-template <typename TIn, int NW, int QZ, int PD, bool IMG, bool LAB>
-__device__ __forceinline__ void fwd_tile_t(const VolConst& vc, int t, const PhiloxKey& key) {
-  const TileCoord tc = tile_coord_flat<NW, QZ>(t, vc.onx, vc.ony, vc.onz);
-  FwdP<TIn> P;
-  P.img = (const TIn*)vc.image;
-  P.lab = vc.label;
-  P.oimg = vc.out_image;
-  P.olab = vc.out_label;
-  P.dx = vc.tq[0][2];
-  P.dy = vc.tq[1][2];
-  P.dz = vc.tq[2][2];
-  P.nx = vc.nx;
-  P.ny = vc.ny;
-  P.nz = vc.nz;
-  P.nxy = vc.nx * vc.ny;
-  P.plane = vc.onx * vc.ony;
-  P.fill_label = vc.fill_label;
-  P.a = vc.a;
-  P.b = vc.b;
-  P.sigma = vc.sigma;
-  P.fill = vc.fill;
-  P.yfill = fmaf(vc.a, vc.fill, vc.b);
-  P.klo = vc.occ_klo;
-  P.khi = vc.occ_khi;
-  P.window = (vc.flags & AUG_FLAG_WINDOW) != 0;
-  const unsigned noise_id = vc.noise_id;
-  const bool noisy = IMG && vc.sigma > 0.0f;
-  const unsigned onx = (unsigned)vc.onx, ony = (unsigned)vc.ony;
-  long long sx = coord_q40(vc.tq[0], tc.ic, tc.jc, tc.k0);
-  long long sy = coord_q40(vc.tq[1], tc.ic, tc.jc, tc.k0);
-  long long sz = coord_q40(vc.tq[2], tc.ic, tc.jc, tc.k0);
-  const long long ds[3] = {P.dx, P.dy, P.dz};
-  const int o = (tc.k0 * vc.ony + tc.jc) * vc.onx + tc.ic;
-  // Occlusion and window are decided per run (the z-range is the same for the
-  // whole CTA): runs that meet neither take the code without them.
-  const bool post = P.window || (P.klo <= P.khi && P.klo < tc.k1 && P.khi >= tc.k0);
-  if (!post) {
-    // One warp vote for the whole z-run; quads are re-classified only when
-    // the run straddles the input boundary.
-    const long long s0[3] = {sx, sy, sz};
-    const int run_mode =
-        warp_mode(classify_run<true>(s0, ds, tc.k1 - 1 - tc.k0, P.nx, P.ny, P.nz));
-    const bool full_run = tc.k1 - tc.k0 == 4 * QZ;
-    int oo = o;
-    if (run_mode == MODE_EXTERIOR) {
-#pragma unroll 1
-      for (int kq = tc.k0; kq < tc.k1; kq += 4) {
-        const int n = min(4, tc.k1 - kq);
-        float z[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        if (noisy)
-          quad_normals(((unsigned long long)(kq >> 2) * ony + (unsigned)tc.jc) * onx +
-                           (unsigned)tc.ic,
-                       noise_id, key, z);
-        fwd_quad_exterior<false, TIn, IMG, LAB>(P, oo, n, tc.valid, z, kq);
-      }
-      return;
-    }
-    if (run_mode == MODE_INTERIOR && full_run) {
-#pragma unroll 1
-      for (int kq = tc.k0; kq < tc.k1; kq += 4) {
-        const unsigned long long quad =
-            ((unsigned long long)(kq >> 2) * ony + (unsigned)tc.jc) * onx + (unsigned)tc.ic;
-        fwd_quad<false, TIn, MODE_INTERIOR, IMG, LAB, true, PD>(
-            P, sx, sy, sz, oo, 4, tc.valid, noisy, quad, noise_id, key, kq);
-      }
-      return;
-    }
-    fwd_quads<false, TIn, QZ, PD, IMG, LAB>(P, tc, sx, sy, sz, o, noisy, onx, ony, noise_id,
-                                            key);
-  } else {
-    fwd_quads<true, TIn, QZ, PD, IMG, LAB>(P, tc, sx, sy, sz, o, noisy, onx, ony, noise_id,
-                                           key);
-  }
-}
-
-template <int NW, int QZ, int PD>
-__device__ __forceinline__ void fwd_tile(const VolConst& vc, int t, const PhiloxKey& key) {
-  const bool img = vc.out_image != nullptr, lab = vc.out_label != nullptr;
-  if (vc.dtype == AUG_I16) {
-    if (img && lab)
-      fwd_tile_t<int16_t, NW, QZ, PD, true, true>(vc, t, key);
-    else if (img)
-      fwd_tile_t<int16_t, NW, QZ, PD, true, false>(vc, t, key);
-    else
-      fwd_tile_t<int16_t, NW, QZ, PD, false, true>(vc, t, key);
-  } else {
-    if (img && lab)
-      fwd_tile_t<float, NW, QZ, PD, true, true>(vc, t, key);
-    else if (img)
-      fwd_tile_t<float, NW, QZ, PD, true, false>(vc, t, key);
-    else
-      fwd_tile_t<float, NW, QZ, PD, false, true>(vc, t, key);
-  }
-}
 
 // MB: minimum resident CTAs per SM requested from the register allocator
 // (1 = no constraint); part of the variant, chosen by measurement.  Tiles are
 // handed out dynamically (counter = the workspace's tile counter, set to the
 // grid size by the prologue), which keeps every SM busy until the last tiles.
-template <int NW, int QZ, int MB, int PD>
+// ZR: interior z-runs reuse the z + 1 plane of taps (ZPlane).
+template <int NW, int QZ, int MB, int PD, bool ZR = false>
 __global__ void __launch_bounds__(NW * 32, MB)
     k_fwd_batched(const aug_volume_desc* __restrict__ descs, int n_vols,
                   const VolConst* __restrict__ tab, const PhiloxKey key,
@@ -351,7 +31,7 @@ __global__ void __launch_bounds__(NW * 32, MB)
   for_each_tile_dynamic<NW, QZ, true>(descs, n_vols, sm, counter, [&](int v, int t, long long) {
     const VolConst& vc = tab[v];
     if (vc.ok && (vc.out_image != nullptr || vc.out_label != nullptr))
-      fwd_tile<NW, QZ, PD>(vc, t, key);
+      fwd_tile<NW, QZ, PD, ZR>(vc, t, key);
   });
 }
 
@@ -377,23 +57,41 @@ struct FwdVariant {
 };
 #define FWD_V(NW, QZ, MB, PD) \
   { NW, QZ, k_fwd_batched<NW, QZ, MB, PD>, k_fwd_volume<NW, QZ, MB, PD> }
+#define FWD_Z(NW, QZ, MB) \
+  { NW, QZ, k_fwd_batched<NW, QZ, MB, 1, true>, k_fwd_volume<NW, QZ, MB, 1> }
 // (warps per CTA, quads per thread, min CTAs per SM, pipeline depth)
 const FwdVariant kFwd[] = {FWD_V(4, 8, 8, 2),  FWD_V(4, 8, 1, 2),  FWD_V(4, 8, 6, 4),
                            FWD_V(4, 8, 8, 1),  FWD_V(4, 8, 12, 1), FWD_V(4, 8, 10, 2),
                            FWD_V(8, 4, 4, 1),  FWD_V(8, 4, 6, 1),  FWD_V(8, 4, 4, 2),
-                           FWD_V(4, 4, 12, 1), FWD_V(2, 8, 16, 1), FWD_V(4, 8, 9, 2)};
+                           FWD_V(4, 4, 12, 1), FWD_V(2, 8, 16, 1), FWD_V(4, 8, 9, 2),
+                           FWD_Z(2, 8, 16),    FWD_Z(4, 8, 8),     FWD_Z(2, 8, 12),
+                           FWD_V(2, 8, 12, 1), FWD_V(2, 8, 10, 1), FWD_Z(2, 8, 10),
+                           FWD_V(2, 8, 12, 2), FWD_V(2, 8, 10, 2), FWD_Z(2, 8, 14)};
 #undef FWD_V
+#undef FWD_Z
 const char* kFwdNames[] = {"t32x4x32_pd2_32w", "t32x4x32_pd2",     "t32x4x32_pd4_24w",
                            "t32x4x32_pd1_32w", "t32x4x32_pd1_48w", "t32x4x32_pd2_40w",
                            "t32x8x16_pd1_32w", "t32x8x16_pd1_48w", "t32x8x16_pd2_32w",
-                           "t32x4x16_pd1_48w", "t32x2x32_pd1_32w", "t32x4x32_pd2_36w"};
+                           "t32x4x16_pd1_48w", "t32x2x32_pd1_32w", "t32x4x32_pd2_36w",
+                           "t32x2x32_pd1_32w_zr", "t32x4x32_pd1_32w_zr", "t32x2x32_pd1_24w_zr",
+                           "t32x2x32_pd1_24w",    "t32x2x32_pd1_20w",    "t32x2x32_pd1_20w_zr",
+                           "t32x2x32_pd2_24w",    "t32x2x32_pd2_20w",    "t32x2x32_pd1_28w_zr"};
 }  // namespace
 
-int fwd_num_variants() { return (int)(sizeof(kFwd) / sizeof(kFwd[0])); }
-const char* fwd_variant_name(int v) { return kFwdNames[v]; }
+constexpr int kDirectVariants = (int)(sizeof(kFwd) / sizeof(kFwd[0]));
+// Direct variant of the plain one-volume-per-launch form when a brick variant
+// is selected (the brick kernel exists only in the batched form).
+constexpr int kDirectDefault = 10;
+
+int fwd_num_variants() { return kDirectVariants + fwd_brick_num_variants(); }
+const char* fwd_variant_name(int v) {
+  return v < kDirectVariants ? kFwdNames[v] : fwd_brick_variant_name(v - kDirectVariants);
+}
 
 cudaError_t launch_fwd_batched(int variant, const aug_volume_desc* d, int n, unsigned k0,
                                unsigned k1, VolConst* tab, WsHeader* ws, cudaStream_t st) {
+  if (variant >= kDirectVariants)
+    return launch_fwd_brick(variant - kDirectVariants, d, n, k0, k1, tab, ws, st);
   const FwdVariant& fv = kFwd[variant];
   if (ws == nullptr) return cudaErrorInvalidValue;
   const int block = fv.nw * 32;
@@ -410,7 +108,7 @@ cudaError_t launch_fwd_batched(int variant, const aug_volume_desc* d, int n, uns
 
 cudaError_t launch_fwd_volume(int variant, const aug_volume_desc& h, unsigned k0, unsigned k1,
                               cudaStream_t st) {
-  const FwdVariant& fv = kFwd[variant];
+  const FwdVariant& fv = kFwd[variant < kDirectVariants ? variant : kDirectDefault];
   // Flat plane mapping (tile_coord_flat): NW*32 plane positions x 4*QZ slices.
   const long long plane = (long long)h.out_nx * h.out_ny;
   const long long tiles = ((plane + fv.nw * 32 - 1) / (fv.nw * 32)) *

@@ -62,6 +62,22 @@ cudaError_t launch_iou(int variant, const aug_volume_desc* d, int n, const float
   return cudaSuccess;
 }
 
+// Batch mean of the per-volume losses (Sec. 5.C averages over the batch): one
+// warp, each lane a fixed stride of volumes in double, then a fixed-order
+// shuffle tree, so the result is reproducible.
+__global__ void k_batch_mean(const float* __restrict__ x, int n, float* out) {
+  double s = 0.0;
+  for (int b = threadIdx.x; b < n; b += 32) s += (double)x[b];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(FULL_MASK, s, o);
+  if (threadIdx.x == 0) *out = (float)(s / (double)n);
+}
+
+cudaError_t launch_batch_mean(const float* x, int n, float* out, cudaStream_t st) {
+  k_batch_mean<<<1, 32, 0, st>>>(x, n, out);
+  return cudaGetLastError();
+}
+
 }  // namespace augk
 
 // ---- allocation-free IOU entry point ----------------------------------------------

@@ -27,6 +27,11 @@ cudaError_t launch_fwd_batched(int variant, const aug_volume_desc* d, int n, uns
                                unsigned k1, VolConst* tab, WsHeader* ws, cudaStream_t st);
 cudaError_t launch_fwd_volume(int variant, const aug_volume_desc& h, unsigned k0, unsigned k1,
                               cudaStream_t st);
+// Shared-memory brick forward (fwd_brick.cu): its own variant numbering.
+int fwd_brick_num_variants();
+const char* fwd_brick_variant_name(int v);
+cudaError_t launch_fwd_brick(int variant, const aug_volume_desc* d, int n, unsigned k0,
+                             unsigned k1, VolConst* tab, WsHeader* ws, cudaStream_t st);
 
 int bwd_num_variants();
 const char* bwd_variant_name(int v);
@@ -43,6 +48,9 @@ cudaError_t launch_iou(int variant, const aug_volume_desc* d, int n, const float
                        int kind, float power, bool logits, float* loss, float* gp,
                        VolConst* tab, double* partials, float2* coefs, WsHeader* ws,
                        cudaStream_t st, int max_grid = 0);
+
+// out[0] = mean of x[0..n-1] (fixed summation order).
+cudaError_t launch_batch_mean(const float* x, int n, float* out, cudaStream_t st);
 
 // Per-volume random parameters into the descriptors (one CTA).
 cudaError_t launch_sample_params(aug_volume_desc* d, int n, const aug_param_spec& sp,

@@ -30,31 +30,47 @@ struct SchedSmem {
   long long next;                 // dynamic schedule: the CTA's current global tile
 };
 
-// Output dims of a descriptor if they are valid, else 0 tiles / 0 voxels (the
-// full descriptor check happens when the volume is staged).  FLAT: tiles of
-// the flat plane mapping (tile_coord_flat), else 32 x NW x 4*QZ boxes.
+// Tile shapes of the schedulers: tiles(onx, ony, onz) per volume.
+//  StdTiles<NW, QZ, FLAT>: the flat plane mapping (tile_coord_flat) when FLAT,
+//    else boxes of 32 x NW x 4*QZ (tile_coord).
+//  BoxTiles<TX, TY, TZ>: boxes of TX x TY x TZ, x fastest, then y, then z.
 template <int NW, int QZ, bool FLAT>
+struct StdTiles {
+  __device__ __forceinline__ static int tiles(int onx, int ony, int onz) {
+    const int per_slab = FLAT ? (onx * ony + NW * 32 - 1) / (NW * 32)
+                              : ((onx + 31) / 32) * ((ony + NW - 1) / NW);
+    return per_slab * ((onz + 4 * QZ - 1) / (4 * QZ));
+  }
+};
+template <int TX, int TY, int TZ>
+struct BoxTiles {
+  __device__ __forceinline__ static int tiles(int onx, int ony, int onz) {
+    return ((onx + TX - 1) / TX) * ((ony + TY - 1) / TY) * ((onz + TZ - 1) / TZ);
+  }
+};
+
+// Output dims of a descriptor if they are valid, else 0 tiles / 0 voxels (the
+// full descriptor check happens when the volume is staged).
+template <typename Tiles>
 __device__ __forceinline__ void volume_counts(const aug_volume_desc* d, int& tiles,
                                               long long& vox) {
   const int onx = d->out_nx, ony = d->out_ny, onz = d->out_nz;
   const bool ok = onx >= 1 && ony >= 1 && onz >= 1 && onx <= MAX_DIM && ony <= MAX_DIM &&
                   onz <= MAX_DIM && (long long)onx * ony * onz < (1LL << 31);
-  const int per_slab = FLAT ? (onx * ony + NW * 32 - 1) / (NW * 32)
-                            : ((onx + 31) / 32) * ((ony + NW - 1) / NW);
-  tiles = ok ? per_slab * ((onz + 4 * QZ - 1) / (4 * QZ)) : 0;
+  tiles = ok ? Tiles::tiles(onx, ony, onz) : 0;
   vox = ok ? (long long)onx * ony * onz : 0;
 }
 
 // Per-volume tile and voxel prefix sums of the chunk of cnt volumes starting
 // at c0, into sm.tile_pre / sm.vox_pre (all threads of the CTA together; the
 // leading barrier protects the previous chunk's readers).
-template <int NW, int QZ, bool FLAT>
+template <int NW, typename Tiles>
 __device__ __forceinline__ void chunk_scan(const aug_volume_desc* __restrict__ descs, int c0,
                                            int cnt, SchedSmem<NW * 32>& sm) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int t = 0;
   long long x = 0;
-  if ((int)threadIdx.x < cnt) volume_counts<NW, QZ, FLAT>(descs + c0 + threadIdx.x, t, x);
+  if ((int)threadIdx.x < cnt) volume_counts<Tiles>(descs + c0 + threadIdx.x, t, x);
   // Inclusive warp scan, then across warps.
   int ti = t;
   long long xi = x;
@@ -102,7 +118,7 @@ __device__ __forceinline__ void for_each_tile(const aug_volume_desc* __restrict_
   long long voxbase = 0;  // output voxels before the chunk
   for (int c0 = 0; c0 < n_vols; c0 += BLOCK) {
     const int cnt = min(BLOCK, n_vols - c0);
-    chunk_scan<NW, QZ, FLAT>(descs, c0, cnt, sm);
+    chunk_scan<NW, StdTiles<NW, QZ, FLAT>>(descs, c0, cnt, sm);
     chunk_begin(c0, cnt);
     const int chunk_tiles = sm.tile_pre[cnt];
     int vi = 0;
@@ -125,12 +141,13 @@ __device__ __forceinline__ void for_each_tile(const aug_volume_desc* __restrict_
 // claimed while the current one is processed (its latency is hidden), and
 // tiles are claimed in increasing order, so the tiles in flight at any time
 // are neighbours, as in the static order.  A CTA without a first tile exits
-// without touching the counter.  body must not synchronise the CTA.
-template <int NW, int QZ, bool FLAT, typename BodyF>
-__device__ __forceinline__ void for_each_tile_dynamic(const aug_volume_desc* __restrict__ descs,
-                                                      int n_vols, SchedSmem<NW * 32>& sm,
-                                                      unsigned long long* counter,
-                                                      BodyF&& body) {
+// without touching the counter.  Every thread of the CTA calls body with the
+// same arguments; body may synchronise the CTA, but must not use sm.
+template <int NW, typename Tiles, typename BodyF>
+__device__ __forceinline__ void for_each_tile_dynamic_t(const aug_volume_desc* __restrict__ descs,
+                                                        int n_vols, SchedSmem<NW * 32>& sm,
+                                                        unsigned long long* counter,
+                                                        BodyF&& body) {
   constexpr int BLOCK = NW * 32;
   if (threadIdx.x == 0) sm.next = blockIdx.x;
   __syncthreads();
@@ -144,7 +161,7 @@ __device__ __forceinline__ void for_each_tile_dynamic(const aug_volume_desc* __r
       cnt = min(BLOCK, n_vols - c0);
       gbase = gend;
       voxbase += chunk_vox;
-      chunk_scan<NW, QZ, FLAT>(descs, c0, cnt, sm);
+      chunk_scan<NW, Tiles>(descs, c0, cnt, sm);
       gend = gbase + sm.tile_pre[cnt];
       chunk_vox = sm.vox_pre[cnt];
       vi = 0;
@@ -159,6 +176,14 @@ __device__ __forceinline__ void for_each_tile_dynamic(const aug_volume_desc* __r
     __syncthreads();
     g = sm.next;
   }
+}
+
+template <int NW, int QZ, bool FLAT, typename BodyF>
+__device__ __forceinline__ void for_each_tile_dynamic(const aug_volume_desc* __restrict__ descs,
+                                                      int n_vols, SchedSmem<NW * 32>& sm,
+                                                      unsigned long long* counter,
+                                                      BodyF&& body) {
+  for_each_tile_dynamic_t<NW, StdTiles<NW, QZ, FLAT>>(descs, n_vols, sm, counter, body);
 }
 
 // Image requirement of a kernel's descriptors: never (IOU), when out_image is

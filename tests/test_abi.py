@@ -86,6 +86,9 @@ def test_host_argument_checks_without_gpu(aw):
     assert L.aug_set_variant(0, 10_000) == aw.AUG_ERR_INVALID_ARG
     assert L.aug_set_variant(7, 0) == aw.AUG_ERR_INVALID_ARG
     assert L.aug_philox4x32_10(None, -1, 0, None, None) == aw.AUG_ERR_INVALID_ARG
+    assert L.aug_loss_batch_mean(None, 1, C.c_void_p(256), None) == aw.AUG_ERR_INVALID_ARG
+    assert L.aug_loss_batch_mean(C.c_void_p(256), 0, C.c_void_p(256), None) == \
+        aw.AUG_ERR_INVALID_ARG
     # A host descriptor with a zero dimension is rejected synchronously.
     h = np.zeros(1, aw.DESC_DTYPE)
     assert L.aug_warp_fwd_volume(h.ctypes.data_as(C.c_void_p), 0, None) == \

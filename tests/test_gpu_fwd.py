@@ -110,6 +110,20 @@ def test_config1_full_size_sampled():
     print(f"config1: sampled 64 x 20000 voxels, label ties {ties}")
 
 
+def test_config1_full_grid_four_volumes():
+    """Every voxel of four of the 64 volumes (the smallest and the largest
+    inputs and two others) of the full batched launch against the oracle."""
+    w = workloads.config1(device="cuda")
+    gi, gl = G.run_fwd(w.vols, w.seed)
+    sizes = [v.image.numel() for v in w.vols]
+    pick = sorted({int(np.argmin(sizes)), int(np.argmax(sizes)), 17, 42})
+    for b in pick:
+        img, lab, tie, _ = ref.warp_fwd(w.vols[b], w.seed)
+        G.check_image(gi[b], img, f"config1 vol {b}")
+        G.check_labels(gl[b], lab, tie, f"config1 vol {b}")
+    print(f"config1: every voxel of volumes {pick}")
+
+
 def test_config4_int16_downscale_sampled():
     w = workloads.config4(device="cuda", n_vols=2)
     gi, gl = G.run_fwd(w.vols, w.seed)
