@@ -494,9 +494,12 @@ def bench_fwd_bwd(args, A, D, dev, stream, seed, world):
     giptr = A.pointer_array(gin, dev)
     gaff = torch.empty((len(vols), 3, 4), device=dev)
     ws = A.make_workspace(len(vols), 0, dev)
-    with torch.cuda.stream(stream):
-        A.aug_autotune(A.OP_BWD, batch, ws, grad_out_ptrs=gptr, grad_in_ptrs=giptr,
-                       grad_affine=gaff, reps=3)
+    if args.bwd_variant >= 0:
+        A.aug_set_variant(A.OP_BWD, args.bwd_variant)
+    else:
+        with torch.cuda.stream(stream):
+            A.aug_autotune(A.OP_BWD, batch, ws, grad_out_ptrs=gptr, grad_in_ptrs=giptr,
+                           grad_affine=gaff, reps=3)
 
     def step():
         A.aug_warp_fwd(batch.d_descs, batch.n, seed, ws)
@@ -810,6 +813,8 @@ def main():
                     default="all", help="time one workload only (profiling runs)")
     ap.add_argument("--variant", type=int, default=-1,
                     help="fixed forward kernel variant (default: the library's default)")
+    ap.add_argument("--bwd-variant", type=int, default=-1,
+                    help="fixed adjoint kernel variant (default: autotuned on the workload)")
     ap.add_argument("--autotune", action="store_true",
                     help="pick the forward variant by timing all of them first")
     ap.add_argument("--no-preroll", action="store_true")

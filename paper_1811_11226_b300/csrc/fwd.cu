@@ -79,8 +79,10 @@ const char* kFwdNames[] = {"t32x4x32_pd2_32w", "t32x4x32_pd2",     "t32x4x32_pd4
 }  // namespace
 
 constexpr int kDirectVariants = (int)(sizeof(kFwd) / sizeof(kFwd[0]));
-// Direct variant of the plain one-volume-per-launch form when a brick variant
-// is selected (the brick kernel exists only in the batched form).
+// Variant of the plain one-volume-per-launch form when the selected batched
+// variant is a tap-reuse or register-budget variant (12 and up) or a brick
+// variant: the one-volume kernel of the variant measured fastest per volume.
+constexpr int kPlainVariants = 12;
 constexpr int kDirectDefault = 10;
 
 int fwd_num_variants() { return kDirectVariants + fwd_brick_num_variants(); }
@@ -108,7 +110,7 @@ cudaError_t launch_fwd_batched(int variant, const aug_volume_desc* d, int n, uns
 
 cudaError_t launch_fwd_volume(int variant, const aug_volume_desc& h, unsigned k0, unsigned k1,
                               cudaStream_t st) {
-  const FwdVariant& fv = kFwd[variant < kDirectVariants ? variant : kDirectDefault];
+  const FwdVariant& fv = kFwd[variant < kPlainVariants ? variant : kDirectDefault];
   // Flat plane mapping (tile_coord_flat): NW*32 plane positions x 4*QZ slices.
   const long long plane = (long long)h.out_nx * h.out_ny;
   const long long tiles = ((plane + fv.nw * 32 - 1) / (fv.nw * 32)) *
