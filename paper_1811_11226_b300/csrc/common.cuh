@@ -47,6 +47,13 @@ struct VolConst {
   int ok;
   int flags;             // AUG_FLAG_* bits
   int occ_klo, occ_khi;  // occluded output z indices k_lo <= k <= k_hi (empty if k_lo > k_hi)
+  // Inverse of the affine, o = ainv s + binv (input coordinate -> output
+  // index), and the half-widths of the output box holding every o whose
+  // sample lies within 1 of a given input voxel on each axis (the gather
+  // adjoint); inv_ok = 0 when |det A| < 1e-6.
+  double ainv[3][3], binv[3];
+  float inv_h[3];
+  int inv_ok;
 };
 
 // Full check of one descriptor (pure).  need_image: an image of a known
@@ -113,6 +120,32 @@ __device__ inline void make_volconst(const aug_volume_desc& d, bool ok, VolConst
     const double lo = ceil((double)d.occ_z0), hi = floor((double)d.occ_z0 + (double)d.occ_dz);
     vc.occ_klo = (int)fmin(fmax(lo, -1.0), 1073741824.0);
     vc.occ_khi = (int)fmin(fmax(hi, -2.0), 1073741824.0);
+  }
+  double A[3][3], b[3];
+  for (int r = 0; r < 3; ++r) {
+    for (int c = 0; c < 3; ++c) A[r][c] = (double)vc.tq[r][c] * 0x1p-40;
+    b[r] = (double)vc.tq[r][3] * 0x1p-40;
+  }
+  const double c00 = A[1][1] * A[2][2] - A[1][2] * A[2][1];
+  const double c01 = A[1][2] * A[2][0] - A[1][0] * A[2][2];
+  const double c02 = A[1][0] * A[2][1] - A[1][1] * A[2][0];
+  const double det = A[0][0] * c00 + A[0][1] * c01 + A[0][2] * c02;
+  vc.inv_ok = fabs(det) > 1e-6 ? 1 : 0;
+  const double id = vc.inv_ok ? 1.0 / det : 0.0;
+  vc.ainv[0][0] = c00 * id;
+  vc.ainv[1][0] = c01 * id;
+  vc.ainv[2][0] = c02 * id;
+  vc.ainv[0][1] = (A[0][2] * A[2][1] - A[0][1] * A[2][2]) * id;
+  vc.ainv[1][1] = (A[0][0] * A[2][2] - A[0][2] * A[2][0]) * id;
+  vc.ainv[2][1] = (A[0][1] * A[2][0] - A[0][0] * A[2][1]) * id;
+  vc.ainv[0][2] = (A[0][1] * A[1][2] - A[0][2] * A[1][1]) * id;
+  vc.ainv[1][2] = (A[0][2] * A[1][0] - A[0][0] * A[1][2]) * id;
+  vc.ainv[2][2] = (A[0][0] * A[1][1] - A[0][1] * A[1][0]) * id;
+  for (int c = 0; c < 3; ++c) {
+    vc.binv[c] = -(vc.ainv[c][0] * b[0] + vc.ainv[c][1] * b[1] + vc.ainv[c][2] * b[2]);
+    // a margin far above the rounding of the box centre (below 1e-3 voxel)
+    vc.inv_h[c] =
+        (float)(fabs(vc.ainv[c][0]) + fabs(vc.ainv[c][1]) + fabs(vc.ainv[c][2])) + 0.02f;
   }
   vc.ok = ok ? 1 : 0;
 }

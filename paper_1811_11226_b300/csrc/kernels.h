@@ -39,6 +39,23 @@ cudaError_t launch_bwd(int variant, const aug_volume_desc* d, int n, const float
                        float* const* gin, float* gaff, VolConst* tab, double* partials,
                        WsHeader* ws, cudaStream_t st);
 
+// Brick adjoint (bwd_brick.cu): its own variant numbering; the kernel only
+// (launch_bwd issues the prologue, the zeroing and the finalize).
+int bwd_brick_num_variants();
+const char* bwd_brick_variant_name(int v);
+cudaError_t launch_bwd_brick(int variant, const aug_volume_desc* d, int n,
+                             const float* const* gout, float* const* gin, bool want_gt,
+                             VolConst* tab, double* partials, WsHeader* ws, cudaStream_t st,
+                             int* grid_out);
+
+// Input-driven gather adjoint for grad_in (bwd_gather.cu); the affine gradient
+// then comes from the output-driven pass of a bwd.cu variant.
+int bwd_gather_num_variants();
+const char* bwd_gather_variant_name(int v);
+cudaError_t launch_bwd_gather(int variant, const aug_volume_desc* d, int n,
+                              const float* const* gout, float* const* gin, VolConst* tab,
+                              WsHeader* ws, cudaStream_t st);
+
 int iou_num_variants();
 const char* iou_variant_name(int v);
 // Overlap loss `kind` (aug_loss_kind) on q = (logits ? softmax(p) : p)^power.

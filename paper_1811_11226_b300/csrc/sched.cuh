@@ -48,13 +48,29 @@ struct BoxTiles {
     return ((onx + TX - 1) / TX) * ((ony + TY - 1) / TY) * ((onz + TZ - 1) / TZ);
   }
 };
+// Boxes of TX x TY x TZ over the INPUT grid of each volume (input-driven
+// kernels); counts input voxels.
+template <int TX, int TY, int TZ>
+struct InBoxTiles : BoxTiles<TX, TY, TZ> {
+  static constexpr bool kInput = true;
+};
+template <typename T, typename = void>
+struct tiles_over_input {
+  static constexpr bool value = false;
+};
+template <typename T>
+struct tiles_over_input<T, decltype((void)T::kInput)> {
+  static constexpr bool value = T::kInput;
+};
 
 // Output dims of a descriptor if they are valid, else 0 tiles / 0 voxels (the
 // full descriptor check happens when the volume is staged).
 template <typename Tiles>
 __device__ __forceinline__ void volume_counts(const aug_volume_desc* d, int& tiles,
                                               long long& vox) {
-  const int onx = d->out_nx, ony = d->out_ny, onz = d->out_nz;
+  constexpr bool in = tiles_over_input<Tiles>::value;
+  const int onx = in ? d->in_nx : d->out_nx, ony = in ? d->in_ny : d->out_ny,
+            onz = in ? d->in_nz : d->out_nz;
   const bool ok = onx >= 1 && ony >= 1 && onz >= 1 && onx <= MAX_DIM && ony <= MAX_DIM &&
                   onz <= MAX_DIM && (long long)onx * ony * onz < (1LL << 31);
   tiles = ok ? Tiles::tiles(onx, ony, onz) : 0;
@@ -108,17 +124,17 @@ __device__ __forceinline__ void chunk_scan(const aug_volume_desc* __restrict__ d
 // increasing global order, with all threads of the CTA together (body may
 // synchronise).  chunk_begin(c0, cnt) runs once per chunk before its tiles
 // (all threads; may synchronise), e.g. to zero per-volume partial sums.
-template <int NW, int QZ, bool FLAT = false, typename ChunkF, typename BodyF>
-__device__ __forceinline__ void for_each_tile(const aug_volume_desc* __restrict__ descs,
-                                              int n_vols, SchedSmem<NW * 32>& sm,
-                                              ChunkF&& chunk_begin, BodyF&& body) {
+template <int NW, typename Tiles, typename ChunkF, typename BodyF>
+__device__ __forceinline__ void for_each_tile_t(const aug_volume_desc* __restrict__ descs,
+                                                int n_vols, SchedSmem<NW * 32>& sm,
+                                                ChunkF&& chunk_begin, BodyF&& body) {
   constexpr int BLOCK = NW * 32;
   const long long G = gridDim.x;
   long long gbase = 0;    // global index of the chunk's first tile
   long long voxbase = 0;  // output voxels before the chunk
   for (int c0 = 0; c0 < n_vols; c0 += BLOCK) {
     const int cnt = min(BLOCK, n_vols - c0);
-    chunk_scan<NW, StdTiles<NW, QZ, FLAT>>(descs, c0, cnt, sm);
+    chunk_scan<NW, Tiles>(descs, c0, cnt, sm);
     chunk_begin(c0, cnt);
     const int chunk_tiles = sm.tile_pre[cnt];
     int vi = 0;
@@ -131,6 +147,13 @@ __device__ __forceinline__ void for_each_tile(const aug_volume_desc* __restrict_
     gbase += chunk_tiles;
     voxbase += sm.vox_pre[cnt];
   }
+}
+
+template <int NW, int QZ, bool FLAT = false, typename ChunkF, typename BodyF>
+__device__ __forceinline__ void for_each_tile(const aug_volume_desc* __restrict__ descs,
+                                              int n_vols, SchedSmem<NW * 32>& sm,
+                                              ChunkF&& chunk_begin, BodyF&& body) {
+  for_each_tile_t<NW, StdTiles<NW, QZ, FLAT>>(descs, n_vols, sm, chunk_begin, body);
 }
 
 // Dynamic form of for_each_tile (same global tile order, same body
