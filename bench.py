@@ -554,8 +554,12 @@ def bench_iou(args, A, dev, stream):
     ws = A.make_workspace(len(vols), 6, dev)
     loss = torch.empty(len(vols), device=dev)
     gp = torch.empty_like(w.p)
-    with torch.cuda.stream(stream):
-        A.aug_autotune(A.OP_IOU, batch, ws, p=w.p, n_classes=6, loss=loss, grad_p=gp, reps=3)
+    if args.iou_variant >= 0:
+        A.aug_set_variant(A.OP_IOU, args.iou_variant)
+    else:
+        with torch.cuda.stream(stream):
+            A.aug_autotune(A.OP_IOU, batch, ws, p=w.p, n_classes=6, loss=loss, grad_p=gp,
+                           reps=3)
     graph = capture(lambda: A.iou_loss_fwd_bwd(batch.d_descs, batch.n, w.p, 6, loss, gp, ws),
                     stream)
     ms = time_graph(graph, max(3, args.steps // 5), args.warmup, stream)
@@ -813,6 +817,8 @@ def main():
                     default="all", help="time one workload only (profiling runs)")
     ap.add_argument("--variant", type=int, default=-1,
                     help="fixed forward kernel variant (default: the library's default)")
+    ap.add_argument("--iou-variant", type=int, default=-1,
+                    help="fixed loss kernel variant (default: autotuned on the workload)")
     ap.add_argument("--bwd-variant", type=int, default=-1,
                     help="fixed adjoint kernel variant (default: autotuned on the workload)")
     ap.add_argument("--autotune", action="store_true",

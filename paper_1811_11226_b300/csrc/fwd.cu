@@ -59,6 +59,8 @@ struct FwdVariant {
   { NW, QZ, k_fwd_batched<NW, QZ, MB, PD>, k_fwd_volume<NW, QZ, MB, PD> }
 #define FWD_Z(NW, QZ, MB) \
   { NW, QZ, k_fwd_batched<NW, QZ, MB, 1, true>, k_fwd_volume<NW, QZ, MB, 1> }
+#define FWD_Z2(NW, QZ, MB) \
+  { NW, QZ, k_fwd_batched<NW, QZ, MB, 2, true>, k_fwd_volume<NW, QZ, MB, 2> }
 // (warps per CTA, quads per thread, min CTAs per SM, pipeline depth)
 const FwdVariant kFwd[] = {FWD_V(4, 8, 8, 2),  FWD_V(4, 8, 1, 2),  FWD_V(4, 8, 6, 4),
                            FWD_V(4, 8, 8, 1),  FWD_V(4, 8, 12, 1), FWD_V(4, 8, 10, 2),
@@ -66,16 +68,19 @@ const FwdVariant kFwd[] = {FWD_V(4, 8, 8, 2),  FWD_V(4, 8, 1, 2),  FWD_V(4, 8, 6
                            FWD_V(4, 4, 12, 1), FWD_V(2, 8, 16, 1), FWD_V(4, 8, 9, 2),
                            FWD_Z(2, 8, 16),    FWD_Z(4, 8, 8),     FWD_Z(2, 8, 12),
                            FWD_V(2, 8, 12, 1), FWD_V(2, 8, 10, 1), FWD_Z(2, 8, 10),
-                           FWD_V(2, 8, 12, 2), FWD_V(2, 8, 10, 2), FWD_Z(2, 8, 14)};
+                           FWD_V(2, 8, 12, 2), FWD_V(2, 8, 10, 2), FWD_Z(2, 8, 14),
+                           FWD_Z2(2, 8, 12),   FWD_Z2(2, 8, 10),   FWD_Z2(4, 8, 6)};
 #undef FWD_V
 #undef FWD_Z
+#undef FWD_Z2
 const char* kFwdNames[] = {"t32x4x32_pd2_32w", "t32x4x32_pd2",     "t32x4x32_pd4_24w",
                            "t32x4x32_pd1_32w", "t32x4x32_pd1_48w", "t32x4x32_pd2_40w",
                            "t32x8x16_pd1_32w", "t32x8x16_pd1_48w", "t32x8x16_pd2_32w",
                            "t32x4x16_pd1_48w", "t32x2x32_pd1_32w", "t32x4x32_pd2_36w",
                            "t32x2x32_pd1_32w_zr", "t32x4x32_pd1_32w_zr", "t32x2x32_pd1_24w_zr",
                            "t32x2x32_pd1_24w",    "t32x2x32_pd1_20w",    "t32x2x32_pd1_20w_zr",
-                           "t32x2x32_pd2_24w",    "t32x2x32_pd2_20w",    "t32x2x32_pd1_28w_zr"};
+                           "t32x2x32_pd2_24w",    "t32x2x32_pd2_20w",    "t32x2x32_pd1_28w_zr",
+                           "t32x2x32_pd2_24w_zr", "t32x2x32_pd2_20w_zr", "t32x4x32_pd2_24w_zr"};
 }  // namespace
 
 constexpr int kDirectVariants = (int)(sizeof(kFwd) / sizeof(kFwd[0]));

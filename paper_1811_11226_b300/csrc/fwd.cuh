@@ -332,7 +332,7 @@ __device__ __forceinline__ void fwd_tile_tc(const VolConst& vc, const TileCoord&
       for (int kq = tc.k0; kq < tc.k1; kq += 4) {
         const unsigned long long quad =
             ((unsigned long long)(kq >> 2) * ony + (unsigned)tc.jc) * onx + (unsigned)tc.ic;
-        fwd_quad<false, TIn, MODE_INTERIOR, IMG, LAB, true, PD, ZR && PD == 1>(
+        fwd_quad<false, TIn, MODE_INTERIOR, IMG, LAB, true, PD, ZR>(
             P, sx, sy, sz, oo, 4, tc.valid, noisy, quad, noise_id, key, kq, zp);
       }
       return;
