@@ -79,7 +79,7 @@ __global__ void k_prepare(const aug_volume_desc* __restrict__ descs, int n_vols,
   if (gin != nullptr) ok &= gin[v] != nullptr;
   if (need_label) ok &= d.label != nullptr;
   VolConst vc;
-  make_volconst(d, ok, vc);
+  make_volconst(d, ok, vc, need == NEED_IMAGE_ALWAYS);
   tab[v] = vc;
   if (!ok) record_error(ws, AUG_ERR_DESCRIPTOR, v);
 }

@@ -86,8 +86,11 @@ __device__ inline bool desc_valid(const aug_volume_desc& d, bool need_image, boo
   return ok;
 }
 
-// Parses one descriptor into per-volume constants (one thread).
-__device__ inline void make_volconst(const aug_volume_desc& d, bool ok, VolConst& vc) {
+// Parses one descriptor into per-volume constants (one thread).  with_inverse:
+// also the inverse affine (double arithmetic, slow on this GPU's FP64 units:
+// only the adjoint's prologue computes it, once per volume, for the gather).
+__device__ inline void make_volconst(const aug_volume_desc& d, bool ok, VolConst& vc,
+                                     bool with_inverse = true) {
 #pragma unroll
   for (int m = 0; m < 12; ++m) {
     const float t = d.affine[m];
@@ -121,6 +124,9 @@ __device__ inline void make_volconst(const aug_volume_desc& d, bool ok, VolConst
     vc.occ_klo = (int)fmin(fmax(lo, -1.0), 1073741824.0);
     vc.occ_khi = (int)fmin(fmax(hi, -2.0), 1073741824.0);
   }
+  vc.inv_ok = 0;
+  vc.ok = ok ? 1 : 0;
+  if (!with_inverse) return;
   double A[3][3], b[3];
   for (int r = 0; r < 3; ++r) {
     for (int c = 0; c < 3; ++c) A[r][c] = (double)vc.tq[r][c] * 0x1p-40;
@@ -147,7 +153,6 @@ __device__ inline void make_volconst(const aug_volume_desc& d, bool ok, VolConst
     vc.inv_h[c] =
         (float)(fabs(vc.ainv[c][0]) + fabs(vc.ainv[c][1]) + fabs(vc.ainv[c][2])) + 0.02f;
   }
-  vc.ok = ok ? 1 : 0;
 }
 
 // ---- Q.40 coordinate helpers ------------------------------------------------

@@ -39,7 +39,8 @@ template <int NW, int QZ, int MB, int PD>
 __global__ void __launch_bounds__(NW * 32, MB)
     k_fwd_volume(const aug_volume_desc desc, const PhiloxKey key) {
   __shared__ VolConst vc;
-  if (threadIdx.x == 0) make_volconst(desc, desc_valid(desc, desc.out_image != nullptr, false), vc);
+  if (threadIdx.x == 0)
+    make_volconst(desc, desc_valid(desc, desc.out_image != nullptr, false), vc, false);
   __syncthreads();
   if (!vc.ok) return;
   fwd_tile<NW, QZ, PD>(vc, blockIdx.x, key);
