@@ -211,7 +211,9 @@ __device__ __forceinline__ void bwd_reduce_tile(BwdShared<NW>& sh, const TileCoo
 
 // Adjoint of one tile whose thread coordinates are tc (any lane mapping), with
 // this tile's 12 affine-gradient sums added to sh.acc in a fixed order.
-template <typename TIn, int NW, bool GIN, bool GT, bool SMEM = false, bool XM = false>
+// QS: runs that straddle the input boundary are re-classified per quad.
+template <typename TIn, int NW, bool GIN, bool GT, bool SMEM = false, bool XM = false,
+          bool QS = false>
 __device__ __forceinline__ void bwd_tile_tc(const VolConst& vc, BwdShared<NW>& sh,
                                             const TileCoord& tc, const float* g, float* gin,
                                             const BrickMap& bm = BrickMap{nullptr, 0, 0, 0}) {
@@ -225,19 +227,39 @@ __device__ __forceinline__ void bwd_tile_tc(const VolConst& vc, BwdShared<NW>& s
   const int mode =
       warp_mode(classify_run<true>(s, ds, tc.k1 - 1 - tc.k0, vc.nx, vc.ny, vc.nz));
   // Exterior cells have all taps equal to the fill value: no gradient at all.
-  if (mode == MODE_INTERIOR)
+  if (mode == MODE_INTERIOR) {
     bwd_run<TIn, MODE_INTERIOR, GIN, GT, SMEM, XM>(vc, tc, s[0], s[1], s[2], g, gin, bm, acc);
-  else if (mode == MODE_GENERAL)
+  } else if (mode == MODE_GENERAL && QS && tc.k1 - tc.k0 > 4) {
+    // A run that straddles the input boundary, re-classified quad by quad:
+    // only the quads that do straddle it take the per-tap checks.
+#pragma unroll 1
+    for (int kq = tc.k0; kq < tc.k1; kq += 4) {
+      TileCoord tq = tc;
+      tq.k0 = kq;
+      tq.k1 = min(kq + 4, tc.k1);
+      const int mq =
+          warp_mode(classify_run<true>(s, ds, tq.k1 - 1 - tq.k0, vc.nx, vc.ny, vc.nz));
+      if (mq == MODE_INTERIOR)
+        bwd_run<TIn, MODE_INTERIOR, GIN, GT, SMEM, XM>(vc, tq, s[0], s[1], s[2], g, gin, bm,
+                                                       acc);
+      else if (mq == MODE_GENERAL)
+        bwd_run<TIn, MODE_GENERAL, GIN, GT, SMEM>(vc, tq, s[0], s[1], s[2], g, gin, bm, acc);
+#pragma unroll
+      for (int r = 0; r < 3; ++r) s[r] += (long long)(tq.k1 - tq.k0) * ds[r];
+    }
+  } else if (mode == MODE_GENERAL) {
     bwd_run<TIn, MODE_GENERAL, GIN, GT, SMEM>(vc, tc, s[0], s[1], s[2], g, gin, bm, acc);
+  }
   if (GT) bwd_reduce_tile<NW>(sh, tc, acc);
 }
 
-template <typename TIn, int NW, int QZ, bool GIN, bool GT, bool SMEM = false, bool XM = false>
+template <typename TIn, int NW, int QZ, bool GIN, bool GT, bool SMEM = false, bool XM = false,
+          bool QS = false>
 __device__ __forceinline__ void bwd_tile(const VolConst& vc, BwdShared<NW>& sh, int t,
                                          const float* g, float* gin,
                                          const BrickMap& bm = BrickMap{nullptr, 0, 0, 0}) {
-  bwd_tile_tc<TIn, NW, GIN, GT, SMEM, XM>(vc, sh, tile_coord<NW, QZ>(t, vc.onx, vc.ony, vc.onz),
-                                          g, gin, bm);
+  bwd_tile_tc<TIn, NW, GIN, GT, SMEM, XM, QS>(
+      vc, sh, tile_coord<NW, QZ>(t, vc.onx, vc.ony, vc.onz), g, gin, bm);
 }
 
 }  // namespace augk

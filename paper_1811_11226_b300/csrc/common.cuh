@@ -12,6 +12,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <cmath>
+
 #include "augwarp.h"
 
 namespace augk {
@@ -89,14 +91,23 @@ __device__ inline bool desc_valid(const aug_volume_desc& d, bool need_image, boo
 // Parses one descriptor into per-volume constants (one thread).  with_inverse:
 // also the inverse affine (double arithmetic, slow on this GPU's FP64 units:
 // only the adjoint's prologue computes it, once per volume, for the gather).
-__device__ inline void make_volconst(const aug_volume_desc& d, bool ok, VolConst& vc,
-                                     bool with_inverse = true) {
+// Also a host function (the plain one-volume launch builds the constants on the
+// host and passes them by value): t * 2^40 is an integer-valued double for
+// every float32 t with |t| <= 2^20, so both conversions below are exact.
+__host__ __device__ inline void make_volconst(const aug_volume_desc& d, bool ok, VolConst& vc,
+                                              bool with_inverse = true) {
 #pragma unroll
   for (int m = 0; m < 12; ++m) {
     const float t = d.affine[m];
     const float lim = ((m & 3) < 3) ? 64.0f : 1048576.0f;
+#ifdef __CUDA_ARCH__
     vc.tq[m >> 2][m & 3] =
         (isfinite(t) && fabsf(t) <= lim) ? __double2ll_rn((double)t * 1099511627776.0) : 0LL;
+#else
+    vc.tq[m >> 2][m & 3] =
+        (std::isfinite(t) && std::fabs(t) <= lim) ? std::llrint((double)t * 1099511627776.0)
+                                                  : 0LL;
+#endif
   }
   vc.image = d.image;
   vc.label = d.label;

@@ -8,7 +8,7 @@
 //    same volume (the input they gather from stays in L2) and all of them
 //    finish together.
 //  * k_fwd_volume: the plain form -- one launch per volume, one CTA per tile,
-//    descriptor passed by value.
+//    the volume's constants passed by value.
 //
 // The per-tile code is in fwd.cuh.  The shared-memory brick kernel and its
 // variants are in fwd_brick.cu; they follow this file's variants in the
@@ -35,14 +35,11 @@ __global__ void __launch_bounds__(NW * 32, MB)
   });
 }
 
+// The volume's constants come by value, built on the host from a descriptor
+// that the host has already checked.
 template <int NW, int QZ, int MB, int PD>
 __global__ void __launch_bounds__(NW * 32, MB)
-    k_fwd_volume(const aug_volume_desc desc, const PhiloxKey key) {
-  __shared__ VolConst vc;
-  if (threadIdx.x == 0)
-    make_volconst(desc, desc_valid(desc, desc.out_image != nullptr, false), vc, false);
-  __syncthreads();
-  if (!vc.ok) return;
+    k_fwd_volume(const VolConst vc, const PhiloxKey key) {
   fwd_tile<NW, QZ, PD>(vc, blockIdx.x, key);
 }
 
@@ -50,7 +47,7 @@ __global__ void __launch_bounds__(NW * 32, MB)
 namespace {
 using FwdBK = void (*)(const aug_volume_desc*, int, const VolConst*, const PhiloxKey,
                        unsigned long long*);
-using FwdVK = void (*)(const aug_volume_desc, const PhiloxKey);
+using FwdVK = void (*)(const VolConst, const PhiloxKey);
 struct FwdVariant {
   int nw, qz;
   FwdBK batched;
@@ -122,7 +119,9 @@ cudaError_t launch_fwd_volume(int variant, const aug_volume_desc& h, unsigned k0
   const long long tiles = ((plane + fv.nw * 32 - 1) / (fv.nw * 32)) *
                           ((h.out_nz + 4 * fv.qz - 1) / (4 * fv.qz));
   if (tiles <= 0 || tiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
-  fv.volume<<<(unsigned)tiles, fv.nw * 32, 0, st>>>(h, philox_schedule(k0, k1));
+  VolConst vc;
+  make_volconst(h, true, vc, false);
+  fv.volume<<<(unsigned)tiles, fv.nw * 32, 0, st>>>(vc, philox_schedule(k0, k1));
   return cudaGetLastError();
 }
 
