@@ -29,29 +29,44 @@ def _many(n, seed0):
     return G.to_device(cases)
 
 
-def test_forward_many_volumes_across_scheduler_chunks():
+def _first_variant(op, prefix):
+    A = G.aw()
+    for v in range(A.aug_num_variants(op)):
+        if A.aug_variant_name(op, v).startswith(prefix):
+            return v
+    raise AssertionError(prefix)
+
+
+@pytest.mark.parametrize("prefix", [None, "brick", "bulk"])
+def test_forward_many_volumes_across_scheduler_chunks(prefix):
+    A = G.aw()
     cases = _many(300, 5000)
     seed = 17
-    gi, gl = G.run_fwd(cases, seed)
+    variant = None if prefix is None else _first_variant(A.OP_FWD, prefix)
+    gi, gl = G.run_fwd(cases, seed, variant=variant)
     for b, v in enumerate(cases):
         img, lab, tie, _ = ref.warp_fwd(v, seed)
-        G.check_image(gi[b], img, f"vol {b}")
-        G.check_labels(gl[b], lab, tie, f"vol {b}")
+        G.check_image(gi[b], img, f"{prefix} vol {b}")
+        G.check_labels(gl[b], lab, tie, f"{prefix} vol {b}")
 
 
-def test_adjoint_many_volumes_across_scheduler_chunks():
+@pytest.mark.parametrize("prefix", [None, "bbrick", "gather"])
+def test_adjoint_many_volumes_across_scheduler_chunks(prefix):
     from test_gpu_bwd import run_bwd
-    cases = [v for v in _many(260, 7000) if v.image.dtype == torch.float32]
+    A = G.aw()
+    cases = [v for v in _many(400, 7000) if v.image.dtype == torch.float32]
+    assert len(cases) > 256
     grads = upstream_grads([v.out_shape for v in cases], seed=3, device="cuda")
-    gin, gaff = run_bwd(cases, grads)
+    variant = None if prefix is None else _first_variant(A.OP_BWD, prefix)
+    gin, gaff = run_bwd(cases, grads, variant=variant)
     floored = 0
     for b, v in enumerate(cases):
         ri, rt, _ = ref.warp_bwd(v, grads[b])
         G.check_grad(gin[b], ri, f"grad_in {b}")
         floor = 1e-7 * G.summand_scale(v, grads[b].cpu().numpy())
         floored += G.check_grad_affine(gaff[b], rt, f"grad_T {b}", floor=floor)
-    print(f"grad_T: {floored} of {len(cases)} volumes had a gradient cancelled below the float32 rounding "
-          "scale of its terms and used that floor")
+    print(f"grad_T: {floored} of {len(cases)} volumes had a gradient cancelled below the "
+          "float32 rounding scale of its terms and used that floor")
 
 
 def test_iou_many_volumes_across_scheduler_chunks():

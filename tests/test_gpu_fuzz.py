@@ -72,8 +72,8 @@ def test_random_batches_adjoint_and_loss(seed):
         G.check_grad(gin[b], ri, f"grad_in {b}")
         floor = 1e-7 * G.summand_scale(v, grads[b].cpu().numpy())
         floored += G.check_grad_affine(gaff[b], rt, f"grad_T {b}", floor=floor)
-    print(f"grad_T: {floored} of {len(cases)} volumes had a gradient cancelled below the float32 rounding "
-          "scale of its terms and used that floor")
+    print(f"grad_T: {floored} of {len(cases)} volumes had a gradient cancelled below the "
+          "float32 rounding scale of its terms and used that floor")
     x = class_logits([v.out_shape for v in cases], seed=seed, device="cuda")
     loss, gx = run_loss(cases, x, 6, 1, 2.0, True)
     rl, rg, _ = ref.warp_loss(cases, x, 6, 1, 2.0, True)
