@@ -253,6 +253,8 @@ const char* kBwdNames[] = {"t32x8x16_atomic",   "t32x4x16_atomic",  "t32x8x8_ato
 }  // namespace
 
 constexpr int kBwdDirect = (int)(sizeof(kBwd) / sizeof(kBwd[0]));
+static_assert(sizeof(kBwdNames) / sizeof(kBwdNames[0]) == sizeof(kBwd) / sizeof(kBwd[0]),
+              "one name per adjoint variant");
 
 // Variants 0 .. kBwdDirect - 1 are the kernels of this file, the following
 // ones the brick adjoint (bwd_brick.cu), then the gather adjoint

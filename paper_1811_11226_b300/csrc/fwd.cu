@@ -21,7 +21,7 @@ namespace augk {
 // (1 = no constraint); part of the variant, chosen by measurement.  Tiles are
 // handed out dynamically (counter = the workspace's tile counter, set to the
 // grid size by the prologue), which keeps every SM busy until the last tiles.
-// ZR: interior z-runs reuse the z + 1 plane of taps (ZPlane).
+// ZR: fully interior z-runs reuse the z + 1 plane of taps (ZPlane).
 template <int NW, int QZ, int MB, int PD, bool ZR = false>
 __global__ void __launch_bounds__(NW * 32, MB)
     k_fwd_batched(const aug_volume_desc* __restrict__ descs, int n_vols,
@@ -67,7 +67,8 @@ const FwdVariant kFwd[] = {FWD_V(4, 8, 8, 2),  FWD_V(4, 8, 1, 2),  FWD_V(4, 8, 6
                            FWD_Z(2, 8, 16),    FWD_Z(4, 8, 8),     FWD_Z(2, 8, 12),
                            FWD_V(2, 8, 12, 1), FWD_V(2, 8, 10, 1), FWD_Z(2, 8, 10),
                            FWD_V(2, 8, 12, 2), FWD_V(2, 8, 10, 2), FWD_Z(2, 8, 14),
-                           FWD_Z2(2, 8, 12),   FWD_Z2(2, 8, 10),   FWD_Z2(4, 8, 6)};
+                           FWD_Z2(2, 8, 12),   FWD_Z2(2, 8, 10),   FWD_Z2(4, 8, 6),
+                           FWD_Z(2, 10, 12)};
 #undef FWD_V
 #undef FWD_Z
 #undef FWD_Z2
@@ -78,10 +79,13 @@ const char* kFwdNames[] = {"t32x4x32_pd2_32w", "t32x4x32_pd2",     "t32x4x32_pd4
                            "t32x2x32_pd1_32w_zr", "t32x4x32_pd1_32w_zr", "t32x2x32_pd1_24w_zr",
                            "t32x2x32_pd1_24w",    "t32x2x32_pd1_20w",    "t32x2x32_pd1_20w_zr",
                            "t32x2x32_pd2_24w",    "t32x2x32_pd2_20w",    "t32x2x32_pd1_28w_zr",
-                           "t32x2x32_pd2_24w_zr", "t32x2x32_pd2_20w_zr", "t32x4x32_pd2_24w_zr"};
+                           "t32x2x32_pd2_24w_zr", "t32x2x32_pd2_20w_zr", "t32x4x32_pd2_24w_zr",
+                           "t32x2x40_pd1_24w_zr"};
 }  // namespace
 
 constexpr int kDirectVariants = (int)(sizeof(kFwd) / sizeof(kFwd[0]));
+static_assert(sizeof(kFwdNames) / sizeof(kFwdNames[0]) == sizeof(kFwd) / sizeof(kFwd[0]),
+              "one name per forward variant");
 // Variant of the plain one-volume-per-launch form when the selected batched
 // variant is a tap-reuse or register-budget variant (12 and up) or a brick
 // variant: the one-volume kernel of the variant measured fastest per volume.

@@ -141,19 +141,24 @@ __device__ __forceinline__ void fwd_quad(const FwdP<TIn>& P, long long& sx, long
                        y1 = (unsigned)(fy + 1) < (unsigned)P.ny;
             const bool z0 = (unsigned)fz < (unsigned)P.nz,
                        z1 = (unsigned)(fz + 1) < (unsigned)P.nz;
-            // Unsigned arithmetic wraps harmlessly far outside; an index is only
-            // dereferenced when its tap lies inside the volume.
-            const unsigned ux = (unsigned)P.nx, uxy = (unsigned)P.nxy;
-            const unsigned b =
-                ((unsigned)fz * (unsigned)P.ny + (unsigned)fy) * ux + (unsigned)fx;
-            if (x0 && y0 && z0) tap[i][0] = ld_val(P.img + b);
-            if (x1 && y0 && z0) tap[i][1] = ld_val(P.img + (b + 1u));
-            if (x0 && y1 && z0) tap[i][2] = ld_val(P.img + (b + ux));
-            if (x1 && y1 && z0) tap[i][3] = ld_val(P.img + (b + ux + 1u));
-            if (x0 && y0 && z1) tap[i][4] = ld_val(P.img + (b + uxy));
-            if (x1 && y0 && z1) tap[i][5] = ld_val(P.img + (b + uxy + 1u));
-            if (x0 && y1 && z1) tap[i][6] = ld_val(P.img + (b + uxy + ux));
-            if (x1 && y1 && z1) tap[i][7] = ld_val(P.img + (b + uxy + ux + 1u));
+            // The cell index is formed in unsigned arithmetic (it wraps harmlessly
+            // far outside) and sign-extended: for every tap inside the volume the
+            // row pointers below plus 0 or 1 address it exactly, and a tap is only
+            // dereferenced when it lies inside.
+            const int b = (int)(((unsigned)fz * (unsigned)P.ny + (unsigned)fy) * (unsigned)P.nx +
+                                (unsigned)fx);
+            const TIn* r00 = P.img + b;
+            const TIn* r10 = r00 + P.nx;
+            const TIn* r01 = r00 + P.nxy;
+            const TIn* r11 = r01 + P.nx;
+            if (x0 && y0 && z0) tap[i][0] = ld_val(r00);
+            if (x1 && y0 && z0) tap[i][1] = ld_val(r00 + 1);
+            if (x0 && y1 && z0) tap[i][2] = ld_val(r10);
+            if (x1 && y1 && z0) tap[i][3] = ld_val(r10 + 1);
+            if (x0 && y0 && z1) tap[i][4] = ld_val(r01);
+            if (x1 && y0 && z1) tap[i][5] = ld_val(r01 + 1);
+            if (x0 && y1 && z1) tap[i][6] = ld_val(r11);
+            if (x1 && y1 && z1) tap[i][7] = ld_val(r11 + 1);
           }
           if (LAB) {
             const int rx = fx + hbx, ry = fy + hby, rz = fz + hbz;
@@ -267,7 +272,8 @@ __device__ __forceinline__ void fwd_quads(const FwdP<TIn>& P, const TileCoord& t
 
 // Direct-gather forward of one tile whose thread coordinates are tc (any
 // lane mapping; the z-run of every thread is tc.k0 .. tc.k1 - 1, at most
-// 4*QZ voxels, starting on a quad boundary).
+// 4*QZ voxels, starting on a quad boundary).  ZR: the z + 1 plane reuse along
+// fully interior runs.
 template <typename TIn, int QZ, int PD, bool IMG, bool LAB, bool ZR = false>
 __device__ __forceinline__ void fwd_tile_tc(const VolConst& vc, const TileCoord& tc,
                                             const PhiloxKey& key) {
@@ -326,15 +332,15 @@ __device__ __forceinline__ void fwd_tile_tc(const VolConst& vc, const TileCoord&
       return;
     }
     if (run_mode == MODE_INTERIOR && full_run) {
+      unsigned long long quad =
+          ((unsigned long long)(tc.k0 >> 2) * ony + (unsigned)tc.jc) * onx + (unsigned)tc.ic;
+      const unsigned long long quad_step = (unsigned long long)onx * ony;
       ZPlane zp;
       zp.base = -0x40000000;  // no previous cell
 #pragma unroll 1
-      for (int kq = tc.k0; kq < tc.k1; kq += 4) {
-        const unsigned long long quad =
-            ((unsigned long long)(kq >> 2) * ony + (unsigned)tc.jc) * onx + (unsigned)tc.ic;
+      for (int kq = tc.k0; kq < tc.k1; kq += 4, quad += quad_step)
         fwd_quad<false, TIn, MODE_INTERIOR, IMG, LAB, true, PD, ZR>(
             P, sx, sy, sz, oo, 4, tc.valid, noisy, quad, noise_id, key, kq, zp);
-      }
       return;
     }
     fwd_quads<false, TIn, QZ, PD, IMG, LAB>(P, tc, sx, sy, sz, o, noisy, onx, ony, noise_id,

@@ -86,6 +86,26 @@ def test_config2_full_size():
     print(f"config2: worst relative grad_in error {worst:.2e}")
 
 
+def test_scatter_variants_config2_two_volumes():
+    """Every scatter variant with the x-merge (plain and per-quad
+    re-classified) against the oracle on two full 128^3 volumes, whose long
+    interior runs take the merge paths; the affine gradient alone too."""
+    A = G.aw()
+    w = workloads.config2(device="cuda", n_vols=2)
+    refs = [ref.warp_bwd(v, w.g[b]) for b, v in enumerate(w.vols)]
+    names = [(v, A.aug_variant_name(A.OP_BWD, v)) for v in range(A.aug_num_variants(A.OP_BWD))]
+    picked = [v for v, nm in names if "atomic_xmerge" in nm]
+    assert len(picked) >= 3
+    for var in picked:
+        gin, gaff = run_bwd(w.vols, w.g, variant=var)
+        _, gt_only = run_bwd(w.vols, w.g, want_gin=False, variant=var)
+        assert np.array_equal(gt_only, gaff), var
+        for b in range(len(w.vols)):
+            ri, rt, _ = refs[b]
+            G.check_grad(gin[b], ri, f"variant {var} config2 grad_in {b}")
+            G.check_grad_affine(gaff[b], rt, f"variant {var} config2 grad_T {b}")
+
+
 def test_int16_affine_gradient():
     # Full-resolution int16 input, 3 mm / 0.7 mm downscale, a smaller crop
     # centred like the full-size one.
