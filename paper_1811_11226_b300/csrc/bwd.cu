@@ -19,7 +19,7 @@
 
 namespace augk {
 
-template <int NW, int QZ, bool GIN, bool GT, bool XM = false, bool QS = false>
+template <int NW, int QZ, bool GIN, bool GT, bool XM = false, bool QS = false, bool PR = false>
 __global__ void __launch_bounds__(NW * 32, 1024 / (NW * 32))
     k_bwd_batched(const aug_volume_desc* __restrict__ descs, int n_vols,
                   const VolConst* __restrict__ tab, const float* const* gout,
@@ -54,9 +54,9 @@ __global__ void __launch_bounds__(NW * 32, 1024 / (NW * 32))
         const float* g = gout[v];
         float* gi = GIN ? gin[v] : nullptr;
         if (vc.dtype == AUG_I16)
-          bwd_tile<int16_t, NW, QZ, GIN, GT, false, XM, QS>(vc, sh, t, g, gi);
+          bwd_tile<int16_t, NW, QZ, GIN, GT, false, XM, QS, PR>(vc, sh, t, g, gi);
         else
-          bwd_tile<float, NW, QZ, GIN, GT, false, XM, QS>(vc, sh, t, g, gi);
+          bwd_tile<float, NW, QZ, GIN, GT, false, XM, QS, PR>(vc, sh, t, g, gi);
       });
   flush();
 }
@@ -230,26 +230,28 @@ struct BwdVariant {
         {k_bwd_batched<NW, QZ, false, false>, k_bwd_batched<NW, QZ, false, true>,      \
          k_bwd_batched<NW, QZ, true, false, true>, k_bwd_batched<NW, QZ, true, true, true> } \
   }
-#define BWD_XQ(NW, QZ)                                                                  \
-  {                                                                                     \
-    NW, QZ, 0,                                                                          \
-        {k_bwd_batched<NW, QZ, false, false>, k_bwd_batched<NW, QZ, false, true, false, true>, \
-         k_bwd_batched<NW, QZ, true, false, true, true>,                                 \
-         k_bwd_batched<NW, QZ, true, true, true, true> }                                 \
+// x-merge with predicated reductions (PR), optionally per-quad re-classified.
+#define BWD_XP(NW, QZ, QS)                                                               \
+  {                                                                                      \
+    NW, QZ, 0,                                                                           \
+        {k_bwd_batched<NW, QZ, false, false>,                                            \
+         k_bwd_batched<NW, QZ, false, true, false, QS>,                                  \
+         k_bwd_batched<NW, QZ, true, false, true, QS, true>,                             \
+         k_bwd_batched<NW, QZ, true, true, true, QS, true> }                             \
   }
 const BwdVariant kBwd[] = {BWD_V(8, 4),         BWD_V(4, 4),        BWD_V(8, 2),
                            BWD_V(8, 8),         BWD_S(16, 2, 24576), BWD_S(8, 2, 16384),
                            BWD_S(8, 4, 24576),  BWD_X(8, 4),        BWD_X(8, 8),
-                           BWD_XQ(8, 8),        BWD_XQ(8, 16)};
+                           BWD_XP(8, 8, false), BWD_XP(8, 8, true), BWD_XP(8, 4, true)};
 #undef BWD_V
 #undef BWD_S
 #undef BWD_X
-#undef BWD_XQ
+#undef BWD_XP
 const char* kBwdNames[] = {"t32x8x16_atomic",   "t32x4x16_atomic",  "t32x8x8_atomic",
                            "t32x8x32_atomic",   "t32x16x8_brick96k", "t32x8x8_brick64k",
                            "t32x8x16_brick96k", "t32x8x16_atomic_xmerge",
-                           "t32x8x32_atomic_xmerge", "t32x8x32_atomic_xmerge_qs",
-                           "t32x8x64_atomic_xmerge_qs"};
+                           "t32x8x32_atomic_xmerge", "t32x8x32_atomic_xmerge_pr",
+                           "t32x8x32_atomic_xmerge_qs_pr", "t32x8x16_atomic_xmerge_qs_pr"};
 }  // namespace
 
 constexpr int kBwdDirect = (int)(sizeof(kBwd) / sizeof(kBwd[0]));

@@ -34,7 +34,10 @@ struct BrickMap {
   int bsy, bsz, boff;
 };
 
-template <typename TIn, int MODE, bool GIN, bool GT, bool SMEM, bool XM = false>
+// PR: every conditional reduction is issued under a predicate inside the
+// instruction and the merges are selects, so the loop body has no divergent
+// branches (no convergence barriers per voxel); the sums are the same.
+template <typename TIn, int MODE, bool GIN, bool GT, bool SMEM, bool XM = false, bool PR = false>
 __device__ __forceinline__ void bwd_run(const VolConst& vc, const TileCoord& tc, long long sx,
                                         long long sy, long long sz,
                                         const float* __restrict__ g, float* __restrict__ gin,
@@ -55,6 +58,8 @@ __device__ __forceinline__ void bwd_run(const VolConst& vc, const TileCoord& tc,
   const int sy_ = SMEM ? bm.bsy : nx, sz_ = SMEM ? bm.bsz : nxy;
   float* const tgt = SMEM ? bm.brick : gin;
 #define RADD(p, v) (SMEM ? red_add_shared((p), (v)) : red_add_global((p), (v)))
+#define RADD_IF(p, v, c) \
+  (SMEM ? red_add_shared_if((p), (v), (c)) : red_add_global_if((p), (v), (c)))
 #pragma unroll 4
   for (int k = tc.k0; k < tc.k1; ++k) {
     // An occluded output voxel is the constant 0: no gradient flows through it.
@@ -65,7 +70,7 @@ __device__ __forceinline__ void bwd_run(const VolConst& vc, const TileCoord& tc,
     // With XM the interior branch runs in every lane of the warp (its shuffles
     // need them all); lanes outside the output only carry zeros and never
     // issue a reduction.
-    if (GIN && (tc.valid || (XM && MODE == MODE_INTERIOR))) {
+    if (GIN && (PR || tc.valid || (XM && MODE == MODE_INTERIOR))) {
       const float wx1 = t.tx, wx0 = 1.0f - t.tx, wy1 = t.ty, wy0 = 1.0f - t.ty;
       const float wz1 = t.tz, wz0 = 1.0f - t.tz;
       const float g00 = ga * wy0 * wz0, g10 = ga * wy1 * wz0;
@@ -74,7 +79,19 @@ __device__ __forceinline__ void bwd_run(const VolConst& vc, const TileCoord& tc,
         const int base = SMEM ? t.fx + t.fy * bm.bsy + t.fz * bm.bsz + bm.boff
                               : (t.fz * ny + t.fy) * nx + t.fx;
         float c0 = g00 * wx0, c1 = g00 * wx1, c2 = g10 * wx0, c3 = g10 * wx1;
-        if (base == pend_base) {
+        if (PR) {
+          const bool merge = base == pend_base;
+          const bool flush = !merge && pend_base >= 0 && tc.valid;
+          float* q = tgt + pend_base;
+          RADD_IF(q, pend[0], flush);
+          RADD_IF(q + 1, pend[1], flush);
+          RADD_IF(q + sy_, pend[2], flush);
+          RADD_IF(q + sy_ + 1, pend[3], flush);
+          c0 = merge ? c0 + pend[0] : c0;
+          c1 = merge ? c1 + pend[1] : c1;
+          c2 = merge ? c2 + pend[2] : c2;
+          c3 = merge ? c3 + pend[3] : c3;
+        } else if (base == pend_base) {
           c0 += pend[0];
           c1 += pend[1];
           c2 += pend[2];
@@ -98,6 +115,15 @@ __device__ __forceinline__ void bwd_run(const VolConst& vc, const TileCoord& tc,
           const float l1 = __shfl_up_sync(FULL_MASK, c1, 1);
           const float l3 = __shfl_up_sync(FULL_MASK, c3, 1);
           const int lg = __shfl_up_sync(FULL_MASK, (int)give, 1);
+          if (PR) {
+            const bool take = lane > 0 && lg;
+            c0 = take ? c0 + l1 : c0;
+            c2 = take ? c2 + l3 : c2;
+            RADD_IF(p, c0, tc.valid);
+            RADD_IF(p + sy_, c2, tc.valid);
+            RADD_IF(p + 1, c1, tc.valid && !give);
+            RADD_IF(p + sy_ + 1, c3, tc.valid && !give);
+          } else {
           if (lane > 0 && lg) {
             c0 += l1;
             c2 += l3;
@@ -110,6 +136,12 @@ __device__ __forceinline__ void bwd_run(const VolConst& vc, const TileCoord& tc,
               RADD(p + sy_ + 1, c3);
             }
           }
+          }
+        } else if (PR) {
+          RADD_IF(p, c0, tc.valid);
+          RADD_IF(p + 1, c1, tc.valid);
+          RADD_IF(p + sy_, c2, tc.valid);
+          RADD_IF(p + sy_ + 1, c3, tc.valid);
         } else {
           RADD(p, c0);
           RADD(p + 1, c1);
@@ -131,6 +163,17 @@ __device__ __forceinline__ void bwd_run(const VolConst& vc, const TileCoord& tc,
                                    : ((unsigned)t.fz * (unsigned)ny + (unsigned)t.fy) *
                                              (unsigned)nx + (unsigned)t.fx;
         const unsigned ux = (unsigned)sy_, uxy = (unsigned)sz_;
+        if (PR) {
+          const bool v = tc.valid;
+          RADD_IF(tgt + base, g00 * wx0, v && x0 && y0 && z0);
+          RADD_IF(tgt + (base + 1u), g00 * wx1, v && x1 && y0 && z0);
+          RADD_IF(tgt + (base + ux), g10 * wx0, v && x0 && y1 && z0);
+          RADD_IF(tgt + (base + ux + 1u), g10 * wx1, v && x1 && y1 && z0);
+          RADD_IF(tgt + (base + uxy), g01 * wx0, v && x0 && y0 && z1);
+          RADD_IF(tgt + (base + uxy + 1u), g01 * wx1, v && x1 && y0 && z1);
+          RADD_IF(tgt + (base + uxy + ux), g11 * wx0, v && x0 && y1 && z1);
+          RADD_IF(tgt + (base + uxy + ux + 1u), g11 * wx1, v && x1 && y1 && z1);
+        } else {
         if (x0 && y0 && z0) RADD(tgt + base, g00 * wx0);
         if (x1 && y0 && z0) RADD(tgt + (base + 1u), g00 * wx1);
         if (x0 && y1 && z0) RADD(tgt + (base + ux), g10 * wx0);
@@ -139,6 +182,7 @@ __device__ __forceinline__ void bwd_run(const VolConst& vc, const TileCoord& tc,
         if (x1 && y0 && z1) RADD(tgt + (base + uxy + 1u), g01 * wx1);
         if (x0 && y1 && z1) RADD(tgt + (base + uxy + ux), g11 * wx0);
         if (x1 && y1 && z1) RADD(tgt + (base + uxy + ux + 1u), g11 * wx1);
+        }
       }
     }
     if (GT) {
@@ -170,6 +214,7 @@ __device__ __forceinline__ void bwd_run(const VolConst& vc, const TileCoord& tc,
     RADD(q + sy_ + 1, pend[3]);
   }
 #undef RADD
+#undef RADD_IF
 }
 
 template <int NW>
@@ -213,7 +258,7 @@ __device__ __forceinline__ void bwd_reduce_tile(BwdShared<NW>& sh, const TileCoo
 // this tile's 12 affine-gradient sums added to sh.acc in a fixed order.
 // QS: runs that straddle the input boundary are re-classified per quad.
 template <typename TIn, int NW, bool GIN, bool GT, bool SMEM = false, bool XM = false,
-          bool QS = false>
+          bool QS = false, bool PR = false>
 __device__ __forceinline__ void bwd_tile_tc(const VolConst& vc, BwdShared<NW>& sh,
                                             const TileCoord& tc, const float* g, float* gin,
                                             const BrickMap& bm = BrickMap{nullptr, 0, 0, 0}) {
@@ -228,7 +273,8 @@ __device__ __forceinline__ void bwd_tile_tc(const VolConst& vc, BwdShared<NW>& s
       warp_mode(classify_run<true>(s, ds, tc.k1 - 1 - tc.k0, vc.nx, vc.ny, vc.nz));
   // Exterior cells have all taps equal to the fill value: no gradient at all.
   if (mode == MODE_INTERIOR) {
-    bwd_run<TIn, MODE_INTERIOR, GIN, GT, SMEM, XM>(vc, tc, s[0], s[1], s[2], g, gin, bm, acc);
+    bwd_run<TIn, MODE_INTERIOR, GIN, GT, SMEM, XM, PR>(vc, tc, s[0], s[1], s[2], g, gin, bm,
+                                                       acc);
   } else if (mode == MODE_GENERAL && QS && tc.k1 - tc.k0 > 4) {
     // A run that straddles the input boundary, re-classified quad by quad:
     // only the quads that do straddle it take the per-tap checks.
@@ -240,25 +286,27 @@ __device__ __forceinline__ void bwd_tile_tc(const VolConst& vc, BwdShared<NW>& s
       const int mq =
           warp_mode(classify_run<true>(s, ds, tq.k1 - 1 - tq.k0, vc.nx, vc.ny, vc.nz));
       if (mq == MODE_INTERIOR)
-        bwd_run<TIn, MODE_INTERIOR, GIN, GT, SMEM, XM>(vc, tq, s[0], s[1], s[2], g, gin, bm,
-                                                       acc);
+        bwd_run<TIn, MODE_INTERIOR, GIN, GT, SMEM, XM, PR>(vc, tq, s[0], s[1], s[2], g, gin, bm,
+                                                           acc);
       else if (mq == MODE_GENERAL)
-        bwd_run<TIn, MODE_GENERAL, GIN, GT, SMEM>(vc, tq, s[0], s[1], s[2], g, gin, bm, acc);
+        bwd_run<TIn, MODE_GENERAL, GIN, GT, SMEM, false, PR>(vc, tq, s[0], s[1], s[2], g, gin,
+                                                             bm, acc);
 #pragma unroll
       for (int r = 0; r < 3; ++r) s[r] += (long long)(tq.k1 - tq.k0) * ds[r];
     }
   } else if (mode == MODE_GENERAL) {
-    bwd_run<TIn, MODE_GENERAL, GIN, GT, SMEM>(vc, tc, s[0], s[1], s[2], g, gin, bm, acc);
+    bwd_run<TIn, MODE_GENERAL, GIN, GT, SMEM, false, PR>(vc, tc, s[0], s[1], s[2], g, gin, bm,
+                                                         acc);
   }
   if (GT) bwd_reduce_tile<NW>(sh, tc, acc);
 }
 
 template <typename TIn, int NW, int QZ, bool GIN, bool GT, bool SMEM = false, bool XM = false,
-          bool QS = false>
+          bool QS = false, bool PR = false>
 __device__ __forceinline__ void bwd_tile(const VolConst& vc, BwdShared<NW>& sh, int t,
                                          const float* g, float* gin,
                                          const BrickMap& bm = BrickMap{nullptr, 0, 0, 0}) {
-  bwd_tile_tc<TIn, NW, GIN, GT, SMEM, XM, QS>(
+  bwd_tile_tc<TIn, NW, GIN, GT, SMEM, XM, QS, PR>(
       vc, sh, tile_coord<NW, QZ>(t, vc.onx, vc.ony, vc.onz), g, gin, bm);
 }
 

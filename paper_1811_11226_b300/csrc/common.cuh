@@ -205,6 +205,21 @@ __device__ __forceinline__ void red_add_shared(float* p, float v) {
                "f"(v)
                : "memory");
 }
+// Predicated forms: the reduction is issued only where pred holds, under a
+// predicate inside the instruction rather than a branch around it (the
+// address is formed either way and must only be valid where pred holds).
+__device__ __forceinline__ void red_add_global_if(float* p, float v, bool pred) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q red.global.add.f32 [%0], %1;\n\t}"
+      ::"l"(p), "f"(v), "r"((int)pred)
+      : "memory");
+}
+__device__ __forceinline__ void red_add_shared_if(float* p, float v, bool pred) {
+  asm volatile(
+      "{\n\t.reg .pred q;\n\tsetp.ne.b32 q, %2, 0;\n\t@q red.shared.add.f32 [%0], %1;\n\t}"
+      ::"r"((unsigned)__cvta_generic_to_shared(p)), "f"(v), "r"((int)pred)
+      : "memory");
+}
 
 // ---- packed FP32 pairs (sm_100+ f32x2 instructions) ----------------------------
 // Two independent float lanes in one 64-bit register; each lane is rounded
