@@ -179,7 +179,7 @@ __global__ void __launch_bounds__(NW * 32)
       partials[((size_t)blockIdx.x * n_vols + staged) * (3 * C) + threadIdx.x] =
           sh.acc[threadIdx.x];
   };
-  for_each_tile<NW, QZ>(
+  for_each_tile<NW, QZ, false, true>(
       descs, n_vols, sm,
       [&](int c0, int cnt) {
         if (SUMS) {

@@ -1,10 +1,11 @@
 // Persistent tile scheduler shared by the batched kernels.
 //
 // The global work list is the concatenation, in batch order, of every
-// volume's output tiles.  CTA b of a grid of G takes global tiles b, b+G,
-// b+2G, ... (static round-robin, so CTAs running at the same time work on
-// neighbouring tiles of the same volume and its input stays in L2), or, in
-// the dynamic form, the next unclaimed tile of that list.
+// volume's output tiles.  In the static form the CTAs take the tiles of each
+// chunk of volumes round-robin (for_each_tile_t), so CTAs
+// running at the same time work on neighbouring tiles of the same volume and
+// its input stays in L2; in the dynamic form a CTA takes the next unclaimed
+// tile of that list.
 //
 // Volumes are processed in chunks of BLOCK (one volume per thread): each
 // thread reads the output dimensions of one descriptor, and a block-wide scan
@@ -124,36 +125,53 @@ __device__ __forceinline__ void chunk_scan(const aug_volume_desc* __restrict__ d
 // increasing global order, with all threads of the CTA together (body may
 // synchronise).  chunk_begin(c0, cnt) runs once per chunk before its tiles
 // (all threads; may synchronise), e.g. to zero per-volume partial sums.
-template <int NW, typename Tiles, typename ChunkF, typename BodyF>
+//
+// The CTAs take a chunk's T tiles round-robin, CTA rank r taking tiles r,
+// r + A, r + 2A, ...; the ranks rotate from chunk to chunk (rank 0 is the CTA
+// after the previous chunk's last worker).  Plain order (BAL = false): A = G,
+// all CTAs.  Balanced order: the chunk takes k = ceil(T / G) rounds and only
+// A = ceil(T / k) CTAs work on it, each on k or k - 1 tiles; with the plain
+// order T = 3.2 G leaves a fourth round of 0.2 G tiles on a fifth of the CTAs,
+// a tail in which each SM holds two or three working CTAs instead of ten.
+// The balanced order pays for memory-bound passes with many CTAs per SM; a
+// latency-bound kernel loses more from the fewer working CTAs.  Either
+// assignment depends only on T and G, so per-CTA partial sums keep a fixed
+// summation order.
+template <int NW, typename Tiles, bool BAL = false, typename ChunkF, typename BodyF>
 __device__ __forceinline__ void for_each_tile_t(const aug_volume_desc* __restrict__ descs,
                                                 int n_vols, SchedSmem<NW * 32>& sm,
                                                 ChunkF&& chunk_begin, BodyF&& body) {
   constexpr int BLOCK = NW * 32;
   const long long G = gridDim.x;
-  long long gbase = 0;    // global index of the chunk's first tile
+  long long rot = 0;      // CTA of rank 0 in the current chunk
   long long voxbase = 0;  // output voxels before the chunk
   for (int c0 = 0; c0 < n_vols; c0 += BLOCK) {
     const int cnt = min(BLOCK, n_vols - c0);
     chunk_scan<NW, Tiles>(descs, c0, cnt, sm);
     chunk_begin(c0, cnt);
-    const int chunk_tiles = sm.tile_pre[cnt];
-    int vi = 0;
-    for (long long g = gbase + ((long long)blockIdx.x - gbase % G + G) % G;
-         g < gbase + chunk_tiles; g += G) {
-      const int lt = (int)(g - gbase);
-      while (sm.tile_pre[vi + 1] <= lt) ++vi;
-      body(c0 + vi, lt - sm.tile_pre[vi], voxbase + sm.vox_pre[vi]);
+    const long long chunk_tiles = sm.tile_pre[cnt];
+    if (chunk_tiles > 0) {
+      const long long rounds = (chunk_tiles + G - 1) / G;
+      const long long active = BAL ? (chunk_tiles + rounds - 1) / rounds : G;
+      const long long r = ((long long)blockIdx.x - rot + G) % G;
+      int vi = 0;
+      if (r < active) {
+        for (long long lt = r; lt < chunk_tiles; lt += active) {
+          while (sm.tile_pre[vi + 1] <= (int)lt) ++vi;
+          body(c0 + vi, (int)lt - sm.tile_pre[vi], voxbase + sm.vox_pre[vi]);
+        }
+      }
+      rot = (rot + (BAL ? active : chunk_tiles)) % G;
     }
-    gbase += chunk_tiles;
     voxbase += sm.vox_pre[cnt];
   }
 }
 
-template <int NW, int QZ, bool FLAT = false, typename ChunkF, typename BodyF>
+template <int NW, int QZ, bool FLAT = false, bool BAL = false, typename ChunkF, typename BodyF>
 __device__ __forceinline__ void for_each_tile(const aug_volume_desc* __restrict__ descs,
                                               int n_vols, SchedSmem<NW * 32>& sm,
                                               ChunkF&& chunk_begin, BodyF&& body) {
-  for_each_tile_t<NW, StdTiles<NW, QZ, FLAT>>(descs, n_vols, sm, chunk_begin, body);
+  for_each_tile_t<NW, StdTiles<NW, QZ, FLAT>, BAL>(descs, n_vols, sm, chunk_begin, body);
 }
 
 // Dynamic form of for_each_tile (same global tile order, same body
