@@ -284,9 +284,10 @@ def run_ours(args, rank, world, local):
         ws = A.make_workspace(batch.n, 6, dev)
         n_out = sum(batch.out_voxels())
         alg = fwd_alg_bytes(w1)
-        if args.variant >= 0:
-            A.aug_set_variant(A.OP_FWD, args.variant)
-            best = args.variant
+        fixed = variant_index(A, A.OP_FWD, args.variant)
+        if fixed >= 0:
+            A.aug_set_variant(A.OP_FWD, fixed)
+            best = fixed
         elif args.autotune:
             with torch.cuda.stream(stream):
                 best, _ = A.aug_autotune(A.OP_FWD, batch, ws, seed=seed, reps=3)
@@ -494,8 +495,8 @@ def bench_fwd_bwd(args, A, D, dev, stream, seed, world):
     giptr = A.pointer_array(gin, dev)
     gaff = torch.empty((len(vols), 3, 4), device=dev)
     ws = A.make_workspace(len(vols), 0, dev)
-    if args.bwd_variant >= 0:
-        A.aug_set_variant(A.OP_BWD, args.bwd_variant)
+    if variant_index(A, A.OP_BWD, args.bwd_variant) >= 0:
+        A.aug_set_variant(A.OP_BWD, variant_index(A, A.OP_BWD, args.bwd_variant))
     else:
         with torch.cuda.stream(stream):
             A.aug_autotune(A.OP_BWD, batch, ws, grad_out_ptrs=gptr, grad_in_ptrs=giptr,
@@ -554,8 +555,8 @@ def bench_iou(args, A, dev, stream):
     ws = A.make_workspace(len(vols), 6, dev)
     loss = torch.empty(len(vols), device=dev)
     gp = torch.empty_like(w.p)
-    if args.iou_variant >= 0:
-        A.aug_set_variant(A.OP_IOU, args.iou_variant)
+    if variant_index(A, A.OP_IOU, args.iou_variant) >= 0:
+        A.aug_set_variant(A.OP_IOU, variant_index(A, A.OP_IOU, args.iou_variant))
     else:
         with torch.cuda.stream(stream):
             A.aug_autotune(A.OP_IOU, batch, ws, p=w.p, n_classes=6, loss=loss, grad_p=gp,
@@ -804,6 +805,17 @@ def run_reference(args, rank, world):
                     "d2h_bytes_per_step": 0}}
 
 
+def variant_index(A, op, spec) -> int:
+    """Index of a kernel variant given as an index or a name (-1: none fixed)."""
+    spec = str(spec)
+    if spec.lstrip("-").isdigit():
+        return int(spec)
+    for v in range(A.aug_num_variants(op)):
+        if A.aug_variant_name(op, v) == spec:
+            return v
+    raise SystemExit(f"unknown variant {spec!r} of op {op}")
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -815,12 +827,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--only", choices=["all", "fwd", "fwd_bwd", "iou", "loss", "train", "smooth"],
                     default="all", help="time one workload only (profiling runs)")
-    ap.add_argument("--variant", type=int, default=-1,
-                    help="fixed forward kernel variant (default: the library's default)")
-    ap.add_argument("--iou-variant", type=int, default=-1,
-                    help="fixed loss kernel variant (default: autotuned on the workload)")
-    ap.add_argument("--bwd-variant", type=int, default=-1,
-                    help="fixed adjoint kernel variant (default: autotuned on the workload)")
+    ap.add_argument("--variant", default="-1",
+                    help="fixed forward kernel variant, by index or name (default: the "
+                         "library's default)")
+    ap.add_argument("--iou-variant", default="-1",
+                    help="fixed loss kernel variant, by index or name (default: autotuned on "
+                         "the workload)")
+    ap.add_argument("--bwd-variant", default="-1",
+                    help="fixed adjoint kernel variant, by index or name (default: autotuned "
+                         "on the workload)")
     ap.add_argument("--autotune", action="store_true",
                     help="pick the forward variant by timing all of them first")
     ap.add_argument("--no-preroll", action="store_true")
