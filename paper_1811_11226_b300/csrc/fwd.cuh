@@ -106,9 +106,11 @@ __device__ __forceinline__ void fwd_quad(const FwdP<TIn>& P, long long& sx, long
           w[i][2] = q40_frac(sz);
         }
         if (MODE == MODE_INTERIOR) {
+          // Interior cells lie inside the input: the index is non-negative, so
+          // the addresses take it zero-extended.
           const int base = (fz * P.ny + fy) * P.nx + fx;
           if (IMG && fetch) {
-            const TIn* p = P.img + base;
+            const TIn* p = P.img + (unsigned)base;
             if (ZR && base == zp.base + P.nxy) {
               tap[i][0] = zp.t[0];
               tap[i][1] = zp.t[1];
@@ -132,7 +134,7 @@ __device__ __forceinline__ void fwd_quad(const FwdP<TIn>& P, long long& sx, long
               zp.t[3] = tap[i][7];
             }
           }
-          if (LAB) lab[i] = __ldg(P.lab + (base + hbx + hby * P.nx + hbz * P.nxy));
+          if (LAB) lab[i] = __ldg(P.lab + (unsigned)(base + hbx + hby * P.nx + hbz * P.nxy));
         } else {
           if (IMG && fetch) {
             const bool x0 = (unsigned)fx < (unsigned)P.nx,
