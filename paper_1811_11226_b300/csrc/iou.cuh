@@ -179,7 +179,11 @@ __global__ void __launch_bounds__(NW * 32)
       partials[((size_t)blockIdx.x * n_vols + staged) * (3 * C) + threadIdx.x] =
           sh.acc[threadIdx.x];
   };
-  for_each_tile<NW, QZ, false, true>(
+  // Balanced tile order for the plain-probability passes (memory-bound); the
+  // p^m and class-score passes, with their special-function work per class,
+  // keep every CTA working (measured: 0.338 / 0.429 ms against 0.344 / 0.448 ms
+  // balanced for the p^2 and softmax^2 IOU steps).
+  for_each_tile<NW, QZ, false, XF == 0>(
       descs, n_vols, sm,
       [&](int c0, int cnt) {
         if (SUMS) {
