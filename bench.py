@@ -20,7 +20,9 @@ Also reported on the same line:
   train_step -- the full-resolution int16 training step: 16 volumes of
                512^2 x 300-600 -> 128x128x160 crops, forward + IOU + affine
                adjoint in one graph (Gvox/s).
-Each of fwd_bwd, iou and train_step carries its own HBM roofline object.
+Each of fwd_bwd, iou and train_step carries its own HBM roofline object;
+their kernel variants are autotuned on their own workloads (the headline
+forward runs the library's default variant unless --variant or --autotune).
 With --all: the single small volume, the loss variants, the training step
 from volumes resampled once to 3 mm, and the anti-aliasing Gaussian.
 
@@ -607,6 +609,27 @@ def bench_loss_variants(args, A, dev, stream):
     return out
 
 
+def tune_step_kernels(A, batch, ws, seed, p, loss, gp, gptr, gaff, stream):
+    """Autotunes the forward, loss and affine-adjoint kernels of a training step
+    on its own workload (as the forward + adjoint and IOU legs do on theirs);
+    returns the chosen variant names and the previous variants, to restore."""
+    ops = (A.OP_FWD, A.OP_IOU, A.OP_BWD)
+    prev = [A.aug_get_variant(op) for op in ops]
+    with torch.cuda.stream(stream):
+        A.aug_autotune(A.OP_FWD, batch, ws, seed=seed, reps=3)
+        A.aug_autotune(A.OP_IOU, batch, ws, p=p, n_classes=6, loss=loss, grad_p=gp, reps=3)
+        A.aug_autotune(A.OP_BWD, batch, ws, grad_out_ptrs=gptr, grad_affine=gaff, reps=3)
+    torch.cuda.synchronize()
+    names = {k: A.aug_variant_name(op, A.aug_get_variant(op))
+             for k, op in zip(("fwd", "loss", "adjoint"), ops)}
+    return names, list(zip(ops, prev))
+
+
+def restore_variants(A, saved):
+    for op, v in saved:
+        A.aug_set_variant(op, v)
+
+
 def bench_train(args, A, dev, stream, seed):
     from synth import workloads
     w = workloads.config4(device=dev, n_vols=args.train_vols)
@@ -623,12 +646,15 @@ def bench_train(args, A, dev, stream, seed):
     gptr = A.pointer_array(w.g, dev)
     gaff = torch.empty((len(vols), 3, 4), device=dev)
 
+    variants, saved = tune_step_kernels(A, batch, ws, seed, w.p, loss, gp, gptr, gaff, stream)
+
     def step():
         A.aug_warp_fwd(batch.d_descs, batch.n, seed, ws)
         A.iou_loss_fwd_bwd(batch.d_descs, batch.n, w.p, 6, loss, gp, ws)
         A.aug_warp_bwd(batch.d_descs, batch.n, gptr, None, gaff, ws)
     graph = capture(step, stream)
     ms = time_graph(graph, max(3, args.steps // 10), args.warmup, stream)
+    restore_variants(A, saved)
     n_out = sum(v.n_out for v in vols)
     alg = 0
     for v in vols:
@@ -643,7 +669,8 @@ def bench_train(args, A, dev, stream, seed):
             "roofline": sub_roofline(alg, ms, "training step (forward, IOU fwd/bwd, affine "
                                      "adjoint) in one graph"),
             "workload": f"{len(vols)} int16 512^2 x 300-600 -> 128x128x160: fwd + IOU fwd/bwd + "
-                        "grad_T"}
+                        "grad_T",
+            "variants": {**variants, "chosen": "autotuned on this workload"}}
 
 
 def bench_train_resampled(args, A, dev, stream, seed):
@@ -697,6 +724,7 @@ def bench_train_resampled(args, A, dev, stream, seed):
     gp = torch.empty_like(w.p)
     gptr = A.pointer_array(w.g, dev)
     gaff = torch.empty((len(w.vols), 3, 4), device=dev)
+    variants, saved = tune_step_kernels(A, batch, ws, seed, w.p, loss, gp, gptr, gaff, stream)
 
     def step():
         A.aug_warp_fwd(batch.d_descs, batch.n, seed, ws)
@@ -704,6 +732,7 @@ def bench_train_resampled(args, A, dev, stream, seed):
         A.aug_warp_bwd(batch.d_descs, batch.n, gptr, None, gaff, ws)
     graph = capture(step, stream)
     ms = time_graph(graph, max(3, args.steps // 10), args.warmup, stream)
+    restore_variants(A, saved)
     st, bad = A.aug_read_device_status(ws)
     if st != 0 or A.aug_read_device_status(rs_ws)[0] != 0 or A.aug_smooth_status() != 0:
         raise RuntimeError("device status after the resampled training step")
@@ -712,7 +741,8 @@ def bench_train_resampled(args, A, dev, stream, seed):
     return {"value": round(n_out / (ms * 1e-3) / 1e9, 3), "unit": "Gvox/s",
             "ms_per_step": round(ms, 4), "one_time_resampling_ms": round(ms_rs, 3),
             "workload": f"{len(w.vols)} int16 512^2 x 300-600 resampled once to 3 mm "
-                        "(smooth + downscale), then fwd + IOU fwd/bwd + grad_T to 128x128x160"}
+                        "(smooth + downscale), then fwd + IOU fwd/bwd + grad_T to 128x128x160",
+            "variants": {**variants, "chosen": "autotuned on this workload"}}
 
 
 def bench_smooth(args, A, dev, stream):

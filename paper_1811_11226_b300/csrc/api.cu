@@ -20,7 +20,7 @@ std::map<std::tuple<int, const void*, int, size_t>, int> g_occ;     // -> CTAs p
 int g_variant[3] = {-1, -1, -1};
 // Defaults: the variants measured fastest on the 64-volume forward batch, the
 // 8 x 128^3 adjoint and the 8 x 120x120x160 loss (6 classes).
-const int kDefaultVariant[3] = {14, 10, 3};
+const int kDefaultVariant[3] = {26, 10, 3};
 
 int current_device() {
   int dev = 0;
@@ -42,7 +42,7 @@ int device_sm_count() {
   return sms;
 }
 
-int persistent_grid(const void* kernel, int block, size_t smem) {
+int persistent_grid(const void* kernel, int block, size_t smem, int cap) {
   const int sms = device_sm_count();
   if (sms <= 0) return 0;
   const int dev = current_device();
@@ -60,7 +60,7 @@ int persistent_grid(const void* kernel, int block, size_t smem) {
       g_occ[key] = per_sm;
     }
   }
-  if (per_sm > kMaxCtasPerSm) per_sm = kMaxCtasPerSm;
+  if (per_sm > cap) per_sm = cap;
   return per_sm * sms;
 }
 

@@ -68,7 +68,7 @@ const FwdVariant kFwd[] = {FWD_V(4, 8, 8, 2),  FWD_V(4, 8, 1, 2),  FWD_V(4, 8, 6
                            FWD_V(2, 8, 12, 1), FWD_V(2, 8, 10, 1), FWD_Z(2, 8, 10),
                            FWD_V(2, 8, 12, 2), FWD_V(2, 8, 10, 2), FWD_Z(2, 8, 14),
                            FWD_Z2(2, 8, 12),   FWD_Z2(2, 8, 10),   FWD_Z2(4, 8, 6),
-                           FWD_Z(2, 10, 12)};
+                           FWD_Z(2, 10, 12),   FWD_Z(1, 8, 24),    FWD_Z(1, 10, 24)};
 #undef FWD_V
 #undef FWD_Z
 #undef FWD_Z2
@@ -80,7 +80,7 @@ const char* kFwdNames[] = {"t32x4x32_pd2_32w", "t32x4x32_pd2",     "t32x4x32_pd4
                            "t32x2x32_pd1_24w",    "t32x2x32_pd1_20w",    "t32x2x32_pd1_20w_zr",
                            "t32x2x32_pd2_24w",    "t32x2x32_pd2_20w",    "t32x2x32_pd1_28w_zr",
                            "t32x2x32_pd2_24w_zr", "t32x2x32_pd2_20w_zr", "t32x4x32_pd2_24w_zr",
-                           "t32x2x40_pd1_24w_zr"};
+                           "t32x2x40_pd1_24w_zr", "t32x1x32_pd1_24w_zr", "t32x1x40_pd1_24w_zr"};
 }  // namespace
 
 constexpr int kDirectVariants = (int)(sizeof(kFwd) / sizeof(kFwd[0]));
@@ -104,7 +104,8 @@ cudaError_t launch_fwd_batched(int variant, const aug_volume_desc* d, int n, uns
   const FwdVariant& fv = kFwd[variant];
   if (ws == nullptr) return cudaErrorInvalidValue;
   const int block = fv.nw * 32;
-  const int grid = persistent_grid((const void*)fv.batched, block, 0);
+  // The forward keeps no per-CTA partials: up to 32 one- or two-warp CTAs per SM.
+  const int grid = persistent_grid((const void*)fv.batched, block, 0, 32);
   if (grid <= 0) return cudaErrorInvalidConfiguration;
   // The prologue sets the tile counter to the grid size: CTA b takes tile b
   // first and claims later tiles from the counter.

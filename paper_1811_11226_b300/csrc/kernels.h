@@ -10,9 +10,11 @@
 
 namespace augk {
 
-// Grid of a persistent launch: (resident CTAs per SM, capped at
-// kMaxCtasPerSm) * SM count of the current device.  Cached per kernel.
-int persistent_grid(const void* kernel, int block, size_t smem);
+// Grid of a persistent launch: (resident CTAs per SM, capped at cap) * SM
+// count of the current device.  Cached per kernel.  The default cap,
+// kMaxCtasPerSm, also sizes the workspace's per-CTA partial sums; kernels
+// that keep none may pass a higher one (at most 32, the SM's CTA limit).
+int persistent_grid(const void* kernel, int block, size_t smem, int cap = kMaxCtasPerSm);
 int device_sm_count();
 
 int fwd_num_variants();
