@@ -22,7 +22,8 @@ Also reported on the same line:
                adjoint in one graph (Gvox/s).
 Each of fwd_bwd, iou and train_step carries its own HBM roofline object;
 their kernel variants are autotuned on their own workloads (the headline
-forward runs the library's default variant unless --variant or --autotune).
+forward runs the library's default variant unless --variant or --autotune;
+--variant also fixes the forward of fwd_bwd).
 With --all: the single small volume, the loss variants, the training step
 from volumes resampled once to 3 mm, and the anti-aliasing Gaussian.
 
@@ -497,18 +498,26 @@ def bench_fwd_bwd(args, A, D, dev, stream, seed, world):
     giptr = A.pointer_array(gin, dev)
     gaff = torch.empty((len(vols), 3, 4), device=dev)
     ws = A.make_workspace(len(vols), 0, dev)
+    # The step's forward kernel is autotuned on this workload too (the
+    # previous choice is restored afterwards), unless a variant is fixed.
+    fwd_prev = A.aug_get_variant(A.OP_FWD)
+    if variant_index(A, A.OP_FWD, args.variant) < 0:
+        with torch.cuda.stream(stream):
+            A.aug_autotune(A.OP_FWD, batch, ws, seed=seed, reps=3)
     if variant_index(A, A.OP_BWD, args.bwd_variant) >= 0:
         A.aug_set_variant(A.OP_BWD, variant_index(A, A.OP_BWD, args.bwd_variant))
     else:
         with torch.cuda.stream(stream):
             A.aug_autotune(A.OP_BWD, batch, ws, grad_out_ptrs=gptr, grad_in_ptrs=giptr,
                            grad_affine=gaff, reps=3)
+    fwd_variant = A.aug_variant_name(A.OP_FWD, A.aug_get_variant(A.OP_FWD))
 
     def step():
         A.aug_warp_fwd(batch.d_descs, batch.n, seed, ws)
         A.aug_warp_bwd(batch.d_descs, batch.n, gptr, giptr, gaff, ws)
     graph = capture(step, stream)
     ms = time_graph(graph, max(3, args.steps // 5), args.warmup, stream)
+    A.aug_set_variant(A.OP_FWD, fwd_prev)
     n_out = sum(v.n_out for v in vols)
     alg = 0
     for v in vols:
@@ -523,7 +532,8 @@ def bench_fwd_bwd(args, A, D, dev, stream, seed, world):
             "alg_GBps": round(alg / (ms * 1e-3) / 1e9, 1),
             "roofline": sub_roofline(alg, ms, "forward + adjoint step (prologue, forward, "
                                      "zeroing, adjoint, finalize)"),
-            "variant": A.aug_variant_name(A.OP_BWD, A.aug_get_variant(A.OP_BWD))}
+            "variant": A.aug_variant_name(A.OP_BWD, A.aug_get_variant(A.OP_BWD)),
+            "fwd_variant": fwd_variant}
 
 
 def bench_config0(args, A, dev, stream, seed):

@@ -35,6 +35,44 @@ __global__ void __launch_bounds__(NW * 32, MB)
   });
 }
 
+// Thread coordinates of box tile t (x fastest, then y, then z): TXW lanes
+// along x, 32 / TXW rows of the warp along y, warps stacked along y; each
+// thread walks 4 * QZ z values.  Exact integer division (one per tile).
+template <int TXW, int NW, int QZ>
+__device__ __forceinline__ TileCoord fwd_box_coord(int t, int onx, int ony, int onz) {
+  constexpr int TX = TXW, TY = (32 / TXW) * NW, TZ = 4 * QZ;
+  const int ntx = (onx + TX - 1) / TX, nty = (ony + TY - 1) / TY;
+  const int q = t / ntx, tx = t - q * ntx, tz = q / nty, ty = q - tz * nty;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  TileCoord c;
+  c.i = tx * TX + lane % TXW;
+  c.j = ty * TY + warp * (32 / TXW) + lane / TXW;
+  c.valid = c.i < onx && c.j < ony;
+  c.ic = min(c.i, onx - 1);
+  c.jc = min(c.j, ony - 1);
+  c.k0 = tz * TZ;
+  c.k1 = min(c.k0 + TZ, onz);
+  return c;
+}
+
+// Box-tiled form: each warp covers TXW x (32 / TXW) output positions (x, y)
+// instead of 32 consecutive positions of a row, so a rotated warp's gathers
+// fall on fewer input lines; stores are TXW-wide row segments.
+template <int TXW, int NW, int QZ, int MB, int PD, bool ZR>
+__global__ void __launch_bounds__(NW * 32, MB)
+    k_fwd_batched_box(const aug_volume_desc* __restrict__ descs, int n_vols,
+                      const VolConst* __restrict__ tab, const PhiloxKey key,
+                      unsigned long long* counter) {
+  __shared__ SchedSmem<NW * 32> sm;
+  for_each_tile_dynamic_t<NW, BoxTiles<TXW, (32 / TXW) * NW, 4 * QZ>>(
+      descs, n_vols, sm, counter, [&](int v, int t, long long) {
+        const VolConst& vc = tab[v];
+        if (vc.ok && (vc.out_image != nullptr || vc.out_label != nullptr))
+          fwd_tile_direct<QZ, PD, ZR>(vc, fwd_box_coord<TXW, NW, QZ>(t, vc.onx, vc.ony, vc.onz),
+                                      key);
+      });
+}
+
 // The volume's constants come by value, built on the host from a descriptor
 // that the host has already checked.
 template <int NW, int QZ, int MB, int PD>
@@ -57,6 +95,8 @@ struct FwdVariant {
   { NW, QZ, k_fwd_batched<NW, QZ, MB, PD>, k_fwd_volume<NW, QZ, MB, PD> }
 #define FWD_Z(NW, QZ, MB) \
   { NW, QZ, k_fwd_batched<NW, QZ, MB, 1, true>, k_fwd_volume<NW, QZ, MB, 1> }
+#define FWD_B(TXW, NW, QZ, MB) \
+  { NW, QZ, k_fwd_batched_box<TXW, NW, QZ, MB, 1, true>, k_fwd_volume<NW, QZ, MB, 1> }
 #define FWD_Z2(NW, QZ, MB) \
   { NW, QZ, k_fwd_batched<NW, QZ, MB, 2, true>, k_fwd_volume<NW, QZ, MB, 2> }
 // (warps per CTA, quads per thread, min CTAs per SM, pipeline depth)
@@ -68,10 +108,14 @@ const FwdVariant kFwd[] = {FWD_V(4, 8, 8, 2),  FWD_V(4, 8, 1, 2),  FWD_V(4, 8, 6
                            FWD_V(2, 8, 12, 1), FWD_V(2, 8, 10, 1), FWD_Z(2, 8, 10),
                            FWD_V(2, 8, 12, 2), FWD_V(2, 8, 10, 2), FWD_Z(2, 8, 14),
                            FWD_Z2(2, 8, 12),   FWD_Z2(2, 8, 10),   FWD_Z2(4, 8, 6),
-                           FWD_Z(2, 10, 12),   FWD_Z(1, 8, 24),    FWD_Z(1, 10, 24)};
+                           FWD_Z(2, 10, 12),   FWD_Z(1, 8, 24),    FWD_Z(1, 10, 24),
+                           FWD_B(8, 1, 10, 24), FWD_B(8, 2, 10, 12), FWD_B(8, 3, 10, 8),
+                           FWD_B(8, 2, 8, 12),  FWD_B(8, 2, 10, 14), FWD_B(8, 1, 10, 28),
+                           FWD_B(8, 2, 8, 14)};
 #undef FWD_V
 #undef FWD_Z
 #undef FWD_Z2
+#undef FWD_B
 const char* kFwdNames[] = {"t32x4x32_pd2_32w", "t32x4x32_pd2",     "t32x4x32_pd4_24w",
                            "t32x4x32_pd1_32w", "t32x4x32_pd1_48w", "t32x4x32_pd2_40w",
                            "t32x8x16_pd1_32w", "t32x8x16_pd1_48w", "t32x8x16_pd2_32w",
@@ -80,7 +124,10 @@ const char* kFwdNames[] = {"t32x4x32_pd2_32w", "t32x4x32_pd2",     "t32x4x32_pd4
                            "t32x2x32_pd1_24w",    "t32x2x32_pd1_20w",    "t32x2x32_pd1_20w_zr",
                            "t32x2x32_pd2_24w",    "t32x2x32_pd2_20w",    "t32x2x32_pd1_28w_zr",
                            "t32x2x32_pd2_24w_zr", "t32x2x32_pd2_20w_zr", "t32x4x32_pd2_24w_zr",
-                           "t32x2x40_pd1_24w_zr", "t32x1x32_pd1_24w_zr", "t32x1x40_pd1_24w_zr"};
+                           "t32x2x40_pd1_24w_zr", "t32x1x32_pd1_24w_zr", "t32x1x40_pd1_24w_zr",
+                           "b8x4x40_pd1_24w_zr",  "b8x8x40_pd1_24w_zr",  "b8x12x40_pd1_24w_zr",
+                           "b8x8x32_pd1_24w_zr",  "b8x8x40_pd1_28w_zr",  "b8x4x40_pd1_28w_zr",
+                           "b8x8x32_pd1_28w_zr"};
 }  // namespace
 
 constexpr int kDirectVariants = (int)(sizeof(kFwd) / sizeof(kFwd[0]));
