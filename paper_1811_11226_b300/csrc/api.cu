@@ -20,7 +20,7 @@ std::map<std::tuple<int, const void*, int, size_t>, int> g_occ;     // -> CTAs p
 int g_variant[3] = {-1, -1, -1};
 // Defaults: the variants measured fastest on the 64-volume forward batch, the
 // 8 x 128^3 adjoint and the 8 x 120x120x160 loss (6 classes).
-const int kDefaultVariant[3] = {33, 10, 3};
+const int kDefaultVariant[3] = {33, 13, 3};
 
 int current_device() {
   int dev = 0;

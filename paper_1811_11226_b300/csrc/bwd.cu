@@ -19,7 +19,8 @@
 
 namespace augk {
 
-template <int NW, int QZ, bool GIN, bool GT, bool XM = false, bool QS = false, bool PR = false>
+template <int NW, int QZ, bool GIN, bool GT, bool XM = false, bool QS = false, bool PR = false,
+          int TXW = 32>
 __global__ void __launch_bounds__(NW * 32, 1024 / (NW * 32))
     k_bwd_batched(const aug_volume_desc* __restrict__ descs, int n_vols,
                   const VolConst* __restrict__ tab, const float* const* gout,
@@ -33,7 +34,7 @@ __global__ void __launch_bounds__(NW * 32, 1024 / (NW * 32))
     if (GT && staged >= 0 && threadIdx.x < 12)
       partials[((size_t)blockIdx.x * n_vols + staged) * 12 + threadIdx.x] = sh.acc[threadIdx.x];
   };
-  for_each_tile<NW, QZ>(
+  for_each_tile_t<NW, BoxTiles<TXW, (32 / TXW) * NW, 4 * QZ>>(
       descs, n_vols, sm,
       [&](int c0, int cnt) {
         // This CTA's partials of the chunk's volumes start at zero (volumes in
@@ -54,9 +55,9 @@ __global__ void __launch_bounds__(NW * 32, 1024 / (NW * 32))
         const float* g = gout[v];
         float* gi = GIN ? gin[v] : nullptr;
         if (vc.dtype == AUG_I16)
-          bwd_tile<int16_t, NW, QZ, GIN, GT, false, XM, QS, PR>(vc, sh, t, g, gi);
+          bwd_tile<int16_t, NW, QZ, GIN, GT, false, XM, QS, PR, TXW>(vc, sh, t, g, gi);
         else
-          bwd_tile<float, NW, QZ, GIN, GT, false, XM, QS, PR>(vc, sh, t, g, gi);
+          bwd_tile<float, NW, QZ, GIN, GT, false, XM, QS, PR, TXW>(vc, sh, t, g, gi);
       });
   flush();
 }
@@ -241,19 +242,34 @@ struct BwdVariant {
          k_bwd_batched<NW, QZ, true, false, true, QS, true>,                             \
          k_bwd_batched<NW, QZ, true, true, true, QS, true> }                             \
   }
+// The same on box patches: each warp covers TXW x (32 / TXW) output positions.
+#define BWD_XPB(TXW, NW, QZ, QS)                                                         \
+  {                                                                                      \
+    NW, QZ, 0,                                                                           \
+        {k_bwd_batched<NW, QZ, false, false>,                                            \
+         k_bwd_batched<NW, QZ, false, true, false, false, false, TXW>,                   \
+         k_bwd_batched<NW, QZ, true, false, true, QS, true, TXW>,                        \
+         k_bwd_batched<NW, QZ, true, true, true, QS, true, TXW> }                        \
+  }
 const BwdVariant kBwd[] = {BWD_V(8, 4),         BWD_V(4, 4),        BWD_V(8, 2),
                            BWD_V(8, 8),         BWD_S(16, 2, 24576), BWD_S(8, 2, 16384),
                            BWD_S(8, 4, 24576),  BWD_X(8, 4),        BWD_X(8, 8),
-                           BWD_XP(8, 8, false), BWD_XP(8, 8, true), BWD_XP(8, 4, true)};
+                           BWD_XP(8, 8, false), BWD_XP(8, 8, true), BWD_XP(8, 4, true),
+                           BWD_XPB(8, 8, 8, true), BWD_XPB(16, 8, 8, true), BWD_XPB(8, 4, 8, true),
+                           BWD_XPB(16, 4, 8, true), BWD_XPB(16, 8, 4, true), BWD_XPB(16, 16, 8, true)};
 #undef BWD_V
 #undef BWD_S
 #undef BWD_X
 #undef BWD_XP
+#undef BWD_XPB
 const char* kBwdNames[] = {"t32x8x16_atomic",   "t32x4x16_atomic",  "t32x8x8_atomic",
                            "t32x8x32_atomic",   "t32x16x8_brick96k", "t32x8x8_brick64k",
                            "t32x8x16_brick96k", "t32x8x16_atomic_xmerge",
                            "t32x8x32_atomic_xmerge", "t32x8x32_atomic_xmerge_pr",
-                           "t32x8x32_atomic_xmerge_qs_pr", "t32x8x16_atomic_xmerge_qs_pr"};
+                           "t32x8x32_atomic_xmerge_qs_pr", "t32x8x16_atomic_xmerge_qs_pr",
+                           "b8x32x32_atomic_xmerge_qs_pr", "b16x16x32_atomic_xmerge_qs_pr",
+                           "b8x16x32_atomic_xmerge_qs_pr", "b16x8x32_atomic_xmerge_qs_pr",
+                           "b16x16x16_atomic_xmerge_qs_pr", "b16x32x32_atomic_xmerge_qs_pr"};
 }  // namespace
 
 constexpr int kBwdDirect = (int)(sizeof(kBwd) / sizeof(kBwd[0]));

@@ -37,7 +37,10 @@ struct BrickMap {
 // PR: every conditional reduction is issued under a predicate inside the
 // instruction and the merges are selects, so the loop body has no divergent
 // branches (no convergence barriers per voxel); the sums are the same.
-template <typename TIn, int MODE, bool GIN, bool GT, bool SMEM, bool XM = false, bool PR = false>
+// TXW: lanes per output row of the warp (32: one row; 8 or 16: box patches);
+// the x-merge hands over only within a row segment.
+template <typename TIn, int MODE, bool GIN, bool GT, bool SMEM, bool XM = false, bool PR = false,
+          int TXW = 32>
 __device__ __forceinline__ void bwd_run(const VolConst& vc, const TileCoord& tc, long long sx,
                                         long long sy, long long sz,
                                         const float* __restrict__ g, float* __restrict__ gin,
@@ -108,15 +111,15 @@ __device__ __forceinline__ void bwd_run(const VolConst& vc, const TileCoord& tc,
           // Merge along x: when the next lane's cell is this one moved by +1
           // in x, this lane's x+1 taps are its x taps; hand the two values
           // over instead of issuing them.
-          const int lane = threadIdx.x & 31;
+          const int lane = threadIdx.x & 31, lx = lane % TXW;
           const int nb = __shfl_down_sync(FULL_MASK, base, 1);
           const int nv = __shfl_down_sync(FULL_MASK, (int)tc.valid, 1);
-          const bool give = tc.valid && lane < 31 && nv && nb == base + 1;
+          const bool give = tc.valid && lx < TXW - 1 && nv && nb == base + 1;
           const float l1 = __shfl_up_sync(FULL_MASK, c1, 1);
           const float l3 = __shfl_up_sync(FULL_MASK, c3, 1);
           const int lg = __shfl_up_sync(FULL_MASK, (int)give, 1);
           if (PR) {
-            const bool take = lane > 0 && lg;
+            const bool take = lx > 0 && lg;
             c0 = take ? c0 + l1 : c0;
             c2 = take ? c2 + l3 : c2;
             RADD_IF(p, c0, tc.valid);
@@ -124,7 +127,7 @@ __device__ __forceinline__ void bwd_run(const VolConst& vc, const TileCoord& tc,
             RADD_IF(p + 1, c1, tc.valid && !give);
             RADD_IF(p + sy_ + 1, c3, tc.valid && !give);
           } else {
-          if (lane > 0 && lg) {
+          if (lx > 0 && lg) {
             c0 += l1;
             c2 += l3;
           }
@@ -258,7 +261,7 @@ __device__ __forceinline__ void bwd_reduce_tile(BwdShared<NW>& sh, const TileCoo
 // this tile's 12 affine-gradient sums added to sh.acc in a fixed order.
 // QS: runs that straddle the input boundary are re-classified per quad.
 template <typename TIn, int NW, bool GIN, bool GT, bool SMEM = false, bool XM = false,
-          bool QS = false, bool PR = false>
+          bool QS = false, bool PR = false, int TXW = 32>
 __device__ __forceinline__ void bwd_tile_tc(const VolConst& vc, BwdShared<NW>& sh,
                                             const TileCoord& tc, const float* g, float* gin,
                                             const BrickMap& bm = BrickMap{nullptr, 0, 0, 0}) {
@@ -273,8 +276,8 @@ __device__ __forceinline__ void bwd_tile_tc(const VolConst& vc, BwdShared<NW>& s
       warp_mode(classify_run<true>(s, ds, tc.k1 - 1 - tc.k0, vc.nx, vc.ny, vc.nz));
   // Exterior cells have all taps equal to the fill value: no gradient at all.
   if (mode == MODE_INTERIOR) {
-    bwd_run<TIn, MODE_INTERIOR, GIN, GT, SMEM, XM, PR>(vc, tc, s[0], s[1], s[2], g, gin, bm,
-                                                       acc);
+    bwd_run<TIn, MODE_INTERIOR, GIN, GT, SMEM, XM, PR, TXW>(vc, tc, s[0], s[1], s[2], g, gin,
+                                                            bm, acc);
   } else if (mode == MODE_GENERAL && QS && tc.k1 - tc.k0 > 4) {
     // A run that straddles the input boundary, re-classified quad by quad:
     // only the quads that do straddle it take the per-tap checks.
@@ -286,8 +289,8 @@ __device__ __forceinline__ void bwd_tile_tc(const VolConst& vc, BwdShared<NW>& s
       const int mq =
           warp_mode(classify_run<true>(s, ds, tq.k1 - 1 - tq.k0, vc.nx, vc.ny, vc.nz));
       if (mq == MODE_INTERIOR)
-        bwd_run<TIn, MODE_INTERIOR, GIN, GT, SMEM, XM, PR>(vc, tq, s[0], s[1], s[2], g, gin, bm,
-                                                           acc);
+        bwd_run<TIn, MODE_INTERIOR, GIN, GT, SMEM, XM, PR, TXW>(vc, tq, s[0], s[1], s[2], g, gin,
+                                                                bm, acc);
       else if (mq == MODE_GENERAL)
         bwd_run<TIn, MODE_GENERAL, GIN, GT, SMEM, false, PR>(vc, tq, s[0], s[1], s[2], g, gin,
                                                              bm, acc);
@@ -302,12 +305,12 @@ __device__ __forceinline__ void bwd_tile_tc(const VolConst& vc, BwdShared<NW>& s
 }
 
 template <typename TIn, int NW, int QZ, bool GIN, bool GT, bool SMEM = false, bool XM = false,
-          bool QS = false, bool PR = false>
+          bool QS = false, bool PR = false, int TXW = 32>
 __device__ __forceinline__ void bwd_tile(const VolConst& vc, BwdShared<NW>& sh, int t,
                                          const float* g, float* gin,
                                          const BrickMap& bm = BrickMap{nullptr, 0, 0, 0}) {
-  bwd_tile_tc<TIn, NW, GIN, GT, SMEM, XM, QS, PR>(
-      vc, sh, tile_coord<NW, QZ>(t, vc.onx, vc.ony, vc.onz), g, gin, bm);
+  bwd_tile_tc<TIn, NW, GIN, GT, SMEM, XM, QS, PR, TXW>(
+      vc, sh, box_tile_coord<TXW, NW, QZ>(t, vc.onx, vc.ony, vc.onz), g, gin, bm);
 }
 
 }  // namespace augk

@@ -35,26 +35,6 @@ __global__ void __launch_bounds__(NW * 32, MB)
   });
 }
 
-// Thread coordinates of box tile t (x fastest, then y, then z): TXW lanes
-// along x, 32 / TXW rows of the warp along y, warps stacked along y; each
-// thread walks 4 * QZ z values.  Exact integer division (one per tile).
-template <int TXW, int NW, int QZ>
-__device__ __forceinline__ TileCoord fwd_box_coord(int t, int onx, int ony, int onz) {
-  constexpr int TX = TXW, TY = (32 / TXW) * NW, TZ = 4 * QZ;
-  const int ntx = (onx + TX - 1) / TX, nty = (ony + TY - 1) / TY;
-  const int q = t / ntx, tx = t - q * ntx, tz = q / nty, ty = q - tz * nty;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  TileCoord c;
-  c.i = tx * TX + lane % TXW;
-  c.j = ty * TY + warp * (32 / TXW) + lane / TXW;
-  c.valid = c.i < onx && c.j < ony;
-  c.ic = min(c.i, onx - 1);
-  c.jc = min(c.j, ony - 1);
-  c.k0 = tz * TZ;
-  c.k1 = min(c.k0 + TZ, onz);
-  return c;
-}
-
 // Box-tiled form: each warp covers TXW x (32 / TXW) output positions (x, y)
 // instead of 32 consecutive positions of a row, so a rotated warp's gathers
 // fall on fewer input lines; stores are TXW-wide row segments.
@@ -68,7 +48,7 @@ __global__ void __launch_bounds__(NW * 32, MB)
       descs, n_vols, sm, counter, [&](int v, int t, long long) {
         const VolConst& vc = tab[v];
         if (vc.ok && (vc.out_image != nullptr || vc.out_label != nullptr))
-          fwd_tile_direct<QZ, PD, ZR>(vc, fwd_box_coord<TXW, NW, QZ>(t, vc.onx, vc.ony, vc.onz),
+          fwd_tile_direct<QZ, PD, ZR>(vc, box_tile_coord<TXW, NW, QZ>(t, vc.onx, vc.ony, vc.onz),
                                       key);
       });
 }

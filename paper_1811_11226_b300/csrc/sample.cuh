@@ -73,6 +73,27 @@ __device__ __forceinline__ TileCoord tile_coord_flat(int t, int onx, int ony, in
   return c;
 }
 
+// Box tiles of TXW x (32 / TXW) * NW x 4 * QZ output voxels (x fastest, then y,
+// then z): TXW lanes along x, 32 / TXW rows of the warp along y, warps stacked
+// along y; each thread walks 4 * QZ z values.  TXW = 32 gives tile_coord's
+// tiles in tile_coord's order.  Exact integer division (once per tile).
+template <int TXW, int NW, int QZ>
+__device__ __forceinline__ TileCoord box_tile_coord(int t, int onx, int ony, int onz) {
+  constexpr int TX = TXW, TY = (32 / TXW) * NW, TZ = 4 * QZ;
+  const int ntx = (onx + TX - 1) / TX, nty = (ony + TY - 1) / TY;
+  const int q = t / ntx, tx = t - q * ntx, tz = q / nty, ty = q - tz * nty;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  TileCoord c;
+  c.i = tx * TX + lane % TXW;
+  c.j = ty * TY + warp * (32 / TXW) + lane / TXW;
+  c.valid = c.i < onx && c.j < ony;
+  c.ic = min(c.i, onx - 1);
+  c.jc = min(c.j, ony - 1);
+  c.k0 = tz * TZ;
+  c.k1 = min(c.k0 + TZ, onz);
+  return c;
+}
+
 // Q.40 coordinate of output voxel (i, j, k) along one axis.
 __device__ __forceinline__ long long coord_q40(const long long (&tq)[4], int i, int j, int k) {
   return tq[0] * (long long)i + tq[1] * (long long)j + tq[2] * (long long)k + tq[3];
