@@ -480,7 +480,8 @@ def run_ours(args, rank, world, local):
         res["antialias_smooth"] = bench_smooth(args, A, dev, stream)
     res["peak"], res["peak_kind"] = peak, peak_kind
     # Each graph replay of the headline step launches two of the library's
-    # kernels: the descriptor prologue (k_prepare) and the forward (k_fwd_batched).
+    # kernels: the descriptor prologue (k_prepare) and the forward (k_fwd_batched or
+    # k_fwd_batched_box, by variant).
     res["launches"] = 2 * args.steps
     return res
 
@@ -946,7 +947,7 @@ def main():
                          "dram__bytes_write.sum of one ncu capture of this kernel variant, "
                          "record lines printed by bench.py --summarize-ncu from that capture's "
                          f"CSV (csrc_hash {kernel_source_hash()})"),
-                     "kernel": res.get("kernel", "k_fwd_batched")},
+                     "kernel": fwd_kernel_name(res["variant"])},
         # The forward is limited by instruction issue, not DRAM: its recorded
         # warp instructions per launch over the measured launch time, against
         # 4 schedulers x SMs x the SM clock sampled during the timed region.
@@ -1027,6 +1028,17 @@ def summarize_ncu(path, kernel_regex=None, variant=None):
             print(f"- csrc_hash: {kernel_source_hash()}")
 
 
+def fwd_kernel_name(variant):
+    """Kernel that a forward variant launches (the variant tables' naming)."""
+    if variant.startswith("b8") or variant.startswith("b16") or variant.startswith("b4"):
+        return "k_fwd_batched_box"
+    if variant.startswith("brick"):
+        return "k_fwd_brick"
+    if variant.startswith("bulk"):
+        return "k_fwd_brick_bulk"
+    return "k_fwd_batched"
+
+
 def issue_roofline(res):
     inst = profile_record("fwd_batched_config1", "warp_inst_per_launch", res["variant"])
     sm_mhz = (res.get("clocks") or {}).get("sm_mhz")
@@ -1037,7 +1049,7 @@ def issue_roofline(res):
     achieved = inst / (res["ms"] * 1e-3) / 1e9
     return {"bound": "issue", "achieved": round(achieved, 1), "peak": round(peak, 1),
             "unit": "G warp inst/s", "frac": round(achieved / peak, 4),
-            "warp_inst_per_launch": int(inst), "kernel": "k_fwd_batched"}
+            "warp_inst_per_launch": int(inst), "kernel": fwd_kernel_name(res["variant"])}
 
 
 def peak_kind_note(kind):
