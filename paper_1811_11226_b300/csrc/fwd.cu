@@ -61,6 +61,14 @@ __global__ void __launch_bounds__(NW * 32, MB)
   fwd_tile<NW, QZ, PD>(vc, blockIdx.x, key);
 }
 
+// The same on box patches (one CTA per box tile).
+template <int TXW, int NW, int QZ, int MB, int PD, bool ZR>
+__global__ void __launch_bounds__(NW * 32, MB)
+    k_fwd_volume_box(const VolConst vc, const PhiloxKey key) {
+  fwd_tile_direct<QZ, PD, ZR>(vc, box_tile_coord<TXW, NW, QZ>(blockIdx.x, vc.onx, vc.ony, vc.onz),
+                              key);
+}
+
 // ---- host launchers ----------------------------------------------------------
 namespace {
 using FwdBK = void (*)(const aug_volume_desc*, int, const VolConst*, const PhiloxKey,
@@ -70,15 +78,19 @@ struct FwdVariant {
   int nw, qz;
   FwdBK batched;
   FwdVK volume;
+  int txw;  // box patches of txw lanes per row (volume kernel too); 0: flat plane mapping
 };
 #define FWD_V(NW, QZ, MB, PD) \
-  { NW, QZ, k_fwd_batched<NW, QZ, MB, PD>, k_fwd_volume<NW, QZ, MB, PD> }
+  { NW, QZ, k_fwd_batched<NW, QZ, MB, PD>, k_fwd_volume<NW, QZ, MB, PD>, 0 }
 #define FWD_Z(NW, QZ, MB) \
-  { NW, QZ, k_fwd_batched<NW, QZ, MB, 1, true>, k_fwd_volume<NW, QZ, MB, 1> }
-#define FWD_B(TXW, NW, QZ, MB) \
-  { NW, QZ, k_fwd_batched_box<TXW, NW, QZ, MB, 1, true>, k_fwd_volume<NW, QZ, MB, 1> }
+  { NW, QZ, k_fwd_batched<NW, QZ, MB, 1, true>, k_fwd_volume<NW, QZ, MB, 1>, 0 }
+#define FWD_B(TXW, NW, QZ, MB)                                     \
+  {                                                                \
+    NW, QZ, k_fwd_batched_box<TXW, NW, QZ, MB, 1, true>,           \
+        k_fwd_volume_box<TXW, NW, QZ, MB, 1, true>, TXW            \
+  }
 #define FWD_Z2(NW, QZ, MB) \
-  { NW, QZ, k_fwd_batched<NW, QZ, MB, 2, true>, k_fwd_volume<NW, QZ, MB, 2> }
+  { NW, QZ, k_fwd_batched<NW, QZ, MB, 2, true>, k_fwd_volume<NW, QZ, MB, 2>, 0 }
 // (warps per CTA, quads per thread, min CTAs per SM, pipeline depth)
 const FwdVariant kFwd[] = {FWD_V(4, 8, 8, 2),  FWD_V(4, 8, 1, 2),  FWD_V(4, 8, 6, 4),
                            FWD_V(4, 8, 8, 1),  FWD_V(4, 8, 12, 1), FWD_V(4, 8, 10, 2),
@@ -114,7 +126,8 @@ constexpr int kDirectVariants = (int)(sizeof(kFwd) / sizeof(kFwd[0]));
 static_assert(sizeof(kFwdNames) / sizeof(kFwdNames[0]) == sizeof(kFwd) / sizeof(kFwd[0]),
               "one name per forward variant");
 // Variant of the plain one-volume-per-launch form when the selected batched
-// variant is a tap-reuse or register-budget variant (12 and up) or a brick
+// variant is a flat-mapped tap-reuse or register-budget variant (12 and up,
+// but not a box variant, whose own one-volume kernel runs) or a brick
 // variant: the one-volume kernel of the variant measured fastest per volume.
 constexpr int kPlainVariants = 12;
 constexpr int kDirectDefault = 10;
@@ -145,11 +158,20 @@ cudaError_t launch_fwd_batched(int variant, const aug_volume_desc* d, int n, uns
 
 cudaError_t launch_fwd_volume(int variant, const aug_volume_desc& h, unsigned k0, unsigned k1,
                               cudaStream_t st) {
-  const FwdVariant& fv = kFwd[variant < kPlainVariants ? variant : kDirectDefault];
-  // Flat plane mapping (tile_coord_flat): NW*32 plane positions x 4*QZ slices.
-  const long long plane = (long long)h.out_nx * h.out_ny;
-  const long long tiles = ((plane + fv.nw * 32 - 1) / (fv.nw * 32)) *
-                          ((h.out_nz + 4 * fv.qz - 1) / (4 * fv.qz));
+  const bool own = variant < kPlainVariants ||
+                   (variant < kDirectVariants && kFwd[variant].txw > 0);
+  const FwdVariant& fv = kFwd[own ? variant : kDirectDefault];
+  long long tiles;
+  if (fv.txw > 0) {
+    // Box patches (box_tile_coord): txw x (32 / txw) * NW positions x 4*QZ slices.
+    const long long tx = fv.txw, ty = (32 / fv.txw) * fv.nw, tz = 4 * fv.qz;
+    tiles = ((h.out_nx + tx - 1) / tx) * ((h.out_ny + ty - 1) / ty) * ((h.out_nz + tz - 1) / tz);
+  } else {
+    // Flat plane mapping (tile_coord_flat): NW*32 plane positions x 4*QZ slices.
+    const long long plane = (long long)h.out_nx * h.out_ny;
+    tiles = ((plane + fv.nw * 32 - 1) / (fv.nw * 32)) *
+            ((h.out_nz + 4 * fv.qz - 1) / (4 * fv.qz));
+  }
   if (tiles <= 0 || tiles > 0x7fffffffLL) return cudaErrorInvalidConfiguration;
   VolConst vc;
   make_volconst(h, true, vc, false);

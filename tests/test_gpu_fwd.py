@@ -61,6 +61,22 @@ def test_all_variants_agree_bitwise(small):
             assert np.array_equal(gl[b], base_l[b]), (v, b)
 
 
+def test_one_volume_launches_agree_bitwise(small):
+    """The one-volume-per-launch form of every direct variant (flat or box
+    tiles) gives the batched output bit for bit."""
+    A = G.aw()
+    seed = 99
+    base_i, base_l = G.run_fwd(small, seed, variant=0)
+    names = [A.aug_variant_name(A.OP_FWD, v) for v in range(A.aug_num_variants(A.OP_FWD))]
+    direct = [v for v, nm in enumerate(names) if nm.startswith(("t32", "b8", "b16"))]
+    assert any(names[v].startswith("b8") for v in direct)
+    for v in direct:
+        gi, gl = G.run_fwd(small, seed, batched=False, variant=v)
+        for b in range(len(small)):
+            assert np.array_equal(gi[b], base_i[b]), (names[v], b)
+            assert np.array_equal(gl[b], base_l[b]), (names[v], b)
+
+
 @pytest.mark.parametrize("dtype", ["float32", "int16"])
 def test_identity_and_integer_shift_are_exact(dtype):
     from synth.phantom import make_phantom
