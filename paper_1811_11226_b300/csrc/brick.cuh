@@ -47,7 +47,7 @@ __device__ __forceinline__ void cp_async_wait_all() {
   asm volatile("cp.async.wait_all;" ::: "memory");
 }
 
-// floor(a / b) for 0 <= a < 2^21 and 1 <= b < 2^24, from the hardware
+// floor(a / b) for 0 <= a < 2^21 and 1 <= b < 2^24 (brick row indices), from the hardware
 // reciprocal (relative error below 2^-23; b is never subnormal): the quotient
 // (a + 1/2) / b lies at least 1/(2b) from an integer, and the reciprocal and
 // the product move it by less than (a + 1/2) 1.5 2^-23 / b < 1/(2b).
@@ -57,34 +57,24 @@ __device__ __forceinline__ int small_div(int a, int b) {
   return (int)(((float)a + 0.5f) * r);
 }
 
-// Box tile t -> (tx, ty, tz), x fastest.
+// Box tile t -> (tx, ty, tz), x fastest (exact integer division: tile indices
+// can exceed the range of small_div on large volumes).
 template <int TX, int TY>
 __device__ __forceinline__ void box_tile_index(int t, int onx, int ony, int& tx, int& ty,
                                                int& tz) {
   const int ntx = (onx + TX - 1) / TX, nty = (ony + TY - 1) / TY;
-  const int q = small_div(t, ntx);
+  const int q = t / ntx;
   tx = t - q * ntx;
-  tz = small_div(q, nty);
+  tz = q / nty;
   ty = q - tz * nty;
 }
 
 // Thread coordinates of box tile t: TXW lanes along x, 32 / TXW rows of the
-// warp along y, warps stacked along y; each thread walks TZ = 4 * QZ z values.
+// warp along y, warps stacked along y; each thread walks TZ = 4 * QZ z values
+// (box_tile_coord).
 template <int TXW, int NW, int QZ>
 __device__ __forceinline__ TileCoord tile_coord_box(int t, int onx, int ony, int onz) {
-  constexpr int TX = TXW, TY = (32 / TXW) * NW, TZ = 4 * QZ;
-  int tx, ty, tz;
-  box_tile_index<TX, TY>(t, onx, ony, tx, ty, tz);
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  TileCoord c;
-  c.i = tx * TX + (lane % TXW);
-  c.j = ty * TY + warp * (32 / TXW) + lane / TXW;
-  c.valid = c.i < onx && c.j < ony;
-  c.ic = min(c.i, onx - 1);
-  c.jc = min(c.j, ony - 1);
-  c.k0 = tz * TZ;
-  c.k1 = min(c.k0 + TZ, onz);
-  return c;
+  return box_tile_coord<TXW, NW, QZ>(t, onx, ony, onz);
 }
 
 // Brick of tile t (warp 0; lanes 8 r + c compute axis r at corner c).  CAP:
